@@ -1,0 +1,138 @@
+"""Seeded synthetic inputs shared by the GPU path's tests/benchmark and the oracle.
+
+This module holds none of the method's arithmetic: it only draws random numbers
+and evaluates the initial-condition formulas of the workloads (fields rho, u,
+phase, B in the layout [nz][ny][nx], x fastest; vectors as [3, nz, ny, nx]).
+Both sides turn these fields into populations with their own code.
+
+Workloads (all in lattice units):
+
+* 3D Taylor-Green vortex (Sec. III.E initial field, x -> 2 pi x / n on node
+  centres, rho = 1).
+* 2D Taylor-Green mode (Sec. III.A initial field; density from the pressure of
+  the exact solution, u_y with the sign that makes the field divergence-free).
+* Periodic box with uniform seeded velocity noise (body-force-driven flow).
+* Hartmann channel (Sec. III.F): walls in y, uniform b = (0, b_y0, 0).
+* Colour-gradient droplets: non-overlapping spheres with a tanh profile.
+* Lid-driven cavity at rest.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def grid(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
+
+
+def taylor_green_3d(n, u0=0.05, rho0=1.0):
+    x, y, z = grid(n, n, n)
+    k = 2.0 * math.pi / n
+    X, Y, Z = k * x, k * y, k * z
+    u = np.stack([u0 * np.cos(X) * np.sin(Y) * np.sin(Z),
+                  -0.5 * u0 * np.sin(X) * np.cos(Y) * np.sin(Z),
+                  -0.5 * u0 * np.sin(X) * np.sin(Y) * np.cos(Z)])
+    rho = np.full((n, n, n), rho0)
+    return rho, u
+
+
+def taylor_green_2d(n, u0=0.01, rho0=1.0, nz=1):
+    """Shear-wave pair in the x-y plane, uniform along z (nz nodes)."""
+    x, y, _ = grid(n, n, nz)
+    k = 2.0 * math.pi / n
+    u = np.stack([u0 * np.cos(k * x) * np.sin(k * y),
+                  -u0 * np.sin(k * x) * np.cos(k * y),
+                  np.zeros_like(x)])
+    rho = rho0 * (1.0 - 0.75 * u0 * u0 * (np.cos(2 * k * x) + np.cos(2 * k * y)))
+    return rho, u
+
+
+def noise_box(shape, amp=1e-3, seed=1, rho0=1.0):
+    """Uniform density, velocity components i.i.d. U(-amp, amp)."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-amp, amp, size=(3, nz, ny, nx))
+    rho = np.full((nz, ny, nx), rho0)
+    return rho, u
+
+
+def random_fields(shape, seed, rho_amp=0.02, u_amp=0.05):
+    """Smooth-free random fields for brute-force parity on tiny grids."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + rng.uniform(-rho_amp, rho_amp, size=(nz, ny, nx))
+    u = rng.uniform(-u_amp, u_amp, size=(3, nz, ny, nx))
+    return rho, u
+
+
+def random_populations(n_cells, seed, spread=0.1):
+    """Arbitrary positive populations, cell-major [n_cells, 19]."""
+    rng = np.random.default_rng(seed)
+    return (1.0 / 19.0) * (1.0 + spread * rng.uniform(-1.0, 1.0, size=(n_cells, 19)))
+
+
+def hartmann(ny, b_y0, nx=1, nz=1):
+    rho = np.ones((nz, ny, nx))
+    u = np.zeros((3, nz, ny, nx))
+    B = np.zeros((3, nz, ny, nx))
+    B[1] = b_y0
+    return rho, u, B
+
+
+def droplets(n, seed=3, r_min=8.0, r_max=24.0, fraction=0.10, width=4.0, gap=4.0, rho_r0=10.0, rho_b0=1.0,
+             max_tries=100000):
+    """Seeded non-overlapping spheres (radius U[r_min, r_max], surface gap >= gap)
+    added until their volume fraction reaches ``fraction`` (the last sphere may
+    overshoot).  phase = tanh(2 (R - r) / width) of the nearest sphere;
+    rho = rho_r0 (1 + phase)/2 + rho_b0 (1 - phase)/2.  Returns (rho, u, phase,
+    spheres, actual_fraction)."""
+    rng = np.random.default_rng(seed)
+    spheres = []
+    vol = 0.0
+    total = float(n) ** 3
+    tries = 0
+    while vol / total < fraction and tries < max_tries:
+        tries += 1
+        r = rng.uniform(r_min, r_max)
+        c = rng.uniform(0, n, size=3)
+        ok = True
+        for (c2, r2) in spheres:
+            d = np.abs(c - c2)
+            d = np.minimum(d, n - d)
+            if math.sqrt(float((d * d).sum())) < r + r2 + gap:
+                ok = False
+                break
+        if ok:
+            spheres.append((c, r))
+            vol += 4.0 / 3.0 * math.pi * r ** 3
+    x, y, z = grid(n, n, n)
+    phase = np.full((n, n, n), -1.0)
+    for (c, r) in spheres:
+        dx = np.abs(x - c[0]); dx = np.minimum(dx, n - dx)
+        dy = np.abs(y - c[1]); dy = np.minimum(dy, n - dy)
+        dz = np.abs(z - c[2]); dz = np.minimum(dz, n - dz)
+        dist = np.sqrt(dx * dx + dy * dy + dz * dz)
+        phase = np.maximum(phase, np.tanh(2.0 * (r - dist) / width))
+    rho = rho_r0 * (1.0 + phase) / 2.0 + rho_b0 * (1.0 - phase) / 2.0
+    u = np.zeros((3, n, n, n))
+    return rho, u, phase, spheres, vol / total
+
+
+def cavity_rest(n):
+    return np.ones((n, n, n)), np.zeros((3, n, n, n))
+
+
+def hartmann_batch(ndomains=64, seed=2, sizes=(32, 48, 64, 96), ha_range=(1.0, 20.0)):
+    """Parameter sweep of cubic Hartmann channels: (n_d, Ha_d) pairs."""
+    rng = np.random.default_rng(seed)
+    n = rng.choice(np.array(sizes), size=ndomains)
+    ha = rng.uniform(ha_range[0], ha_range[1], size=ndomains)
+    return [(int(a), float(b)) for a, b in zip(n, ha)]
+
+
+def cavity_reynolds(count, seed=4, lo=100.0, hi=1000.0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=count)
