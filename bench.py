@@ -1,0 +1,343 @@
+"""Throughput benchmark of the D3Q19 central-moment LBM step on GB300.
+
+Workload: body-force-driven periodic flow on a 512^3 grid (uniform g = 1e-6
+along x, initial u = seeded uniform noise of amplitude 1e-3, rho = 1,
+tau = 0.6), FP32 population storage.  One benchmark "step" is one full LBM
+time step of the whole grid (stream + moments + CM collision with forcing +
+back-transform + store), i.e. 512^3 lattice updates.  The state (2 x 10.2 GB)
+is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload on its own GPU (weak scaling; the single-domain step
+has no data-parallel exchange in this build).
+
+``--impl reference`` times the FP64 CPU oracle (the slow, obviously-correct
+implementation written from the paper) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2010_01628_gb300 import inputs  # noqa: E402
+
+METRIC = "D3Q19 CM-LBM MLUPS & % HBM roofline; time to 1e-6 residual, warm vs cold"
+N = 512
+TAU = 0.6
+G = (1e-6, 0.0, 0.0)
+BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+DTYPE_NAME = {"fp64": "f64", "fp32": "f32", "fp16": "f16 storage / f32 math", "bf16": "bf16 storage / f32 math"}
+
+
+def workload_config(n, precision):
+    return {"workload": f"periodic body-force flow {n}^3, g=1e-6 x, u noise 1e-3 (seed 1), tau=0.6",
+            "grid": [n, n, n], "precision": precision, "lattice": "D3Q19", "streaming": "pull A-B",
+            "l2": "state larger than L2 (no flush needed)", "synthetic": True}
+
+
+def algorithmic_bytes(n, precision):
+    """19 populations read + 19 written per lattice update (no coupled fields)."""
+    return 19 * 2 * BYTES_PER_VALUE[precision] * n ** 3
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (matched by hash); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        ent = d[kernel_key]
+    except Exception:
+        return None
+    try:
+        from paper_2010_01628_gb300 import build
+        if ent.get("source_sha") != build.source_hash():
+            return None
+    except Exception:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.proc = None
+        self.device_id = device_id
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_device_id(torch):
+    try:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        uuid = str(getattr(props, "uuid", "") or "")
+        if uuid:
+            return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    return vis.split(",")[0] if vis else "0"
+
+
+def cpu_baseline_sample(seconds=15.0, n_full=N):
+    """Time the FP64 oracle (closed form, all host threads) on a bounded cubic
+    sample of the workload; returns a cpu_baseline dict (MLUPS)."""
+    import oracle as O
+    cores = O.max_threads()
+    rho, u = inputs.noise_box((64, 64, 64), amp=1e-3, seed=1)
+    d = O.Domain((64, 64, 64), 1 / TAU, g=G)
+    d.init(rho, u)
+    t = time.perf_counter()
+    d.step(2)
+    rate = 64 ** 3 * 2 / (time.perf_counter() - t)  # cell updates / s
+    n = 96
+    steps = max(3, int(seconds * rate / n ** 3))
+    rho, u = inputs.noise_box((n, n, n), amp=1e-3, seed=1)
+    d = O.Domain((n, n, n), 1 / TAU, g=G)
+    d.init(rho, u)
+    t = time.perf_counter()
+    d.step(steps)
+    dt = time.perf_counter() - t
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n}^3 periodic sample of the {n_full}^3 body-force workload, {steps} FP64 steps "
+                      f"(closed-form oracle, OpenMP), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is one oracle step on a
+    bounded cubic sample of the workload, sized so the run takes minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    cores = O.max_threads()
+    rho, u = inputs.noise_box((48, 48, 48), amp=1e-3, seed=1)
+    d = O.Domain((48, 48, 48), 1 / TAU, g=G)
+    d.init(rho, u)
+    t = time.perf_counter()
+    d.step(1)
+    rate = 48 ** 3 / (time.perf_counter() - t)
+    budget = 90.0 / max(1, args.steps + args.warmup)  # seconds per step
+    n = int(max(16, min(256, round((rate * budget) ** (1 / 3) / 8) * 8)))
+    rho, u = inputs.noise_box((n, n, n), amp=1e-3, seed=1)
+    d = O.Domain((n, n, n), 1 / TAU, g=G)
+    d.init(rho, u)
+    d.step(args.warmup)
+    t = time.perf_counter()
+    d.step(args.steps)
+    dt = time.perf_counter() - t
+    value = n ** 3 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(N, "fp64") | {"sample": f"{n}^3"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{n}^3 periodic sample of the {N}^3 workload per step"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(L, torch, ctx, steps, stream):
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    L.lbm_step(ctx, steps)
+    stop.record(stream)
+    stop.synchronize()
+    return start.elapsed_time(stop) / 1e3
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2010_01628_gb300 import binding as L
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n, prec = args.n, args.precision
+    stream = torch.cuda.current_stream()
+    rho, u = inputs.noise_box((n, n, n), amp=1e-3, seed=1)
+    ctx = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=prec)
+    L.lbm_init_fields(ctx, rho, u)
+    L.lbm_step(ctx, args.warmup)
+    barrier()
+    with ClockSampler(smi_device_id(torch)) as clk:
+        barrier()
+        t_dev = time_steps(L, torch, ctx, args.steps, stream)
+        barrier()
+    t_dev = max_over_ranks(t_dev)
+    cells = n ** 3
+    value = world * cells * args.steps / t_dev / 1e6
+    launch_s = t_dev / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = algorithmic_bytes(n, prec) / launch_s / 1e9
+    traffic = committed_traffic(f"fluid_step_{prec}_{n}")
+    L.lbm_reduce(ctx)  # divergence check of the timed run (raises on NaN)
+    L.lbm_destroy(ctx)
+
+    # Other storage precisions of the same workload (short runs, same method).
+    variants = {}
+    if not args.no_variants:
+        for vp in ("fp64", "fp16", "bf16"):
+            if vp == prec:
+                continue
+            vsteps = max(10, args.steps // 10)
+            c2 = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=vp)
+            L.lbm_init_fields(c2, rho, u)
+            L.lbm_step(c2, 3)
+            barrier()
+            tv = max_over_ranks(time_steps(L, torch, c2, vsteps, stream))
+            L.lbm_destroy(c2)
+            torch.cuda.empty_cache()
+            ach = algorithmic_bytes(n, vp) / (tv / vsteps) / 1e9
+            variants[vp] = {"MLUPS": world * cells * vsteps / tv / 1e6, "steps": vsteps,
+                            "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak}
+
+    # End to end through the C ABI with host buffers: upload the initial
+    # fields from pinned host memory, K steps, read the fields back.
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(rho).pin_memory()
+        u_h = torch.from_numpy(u).pin_memory()
+        rho_o = torch.empty_like(rho_h).pin_memory()
+        u_o = torch.empty_like(u_h).pin_memory()
+        c3 = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=prec)
+        barrier()
+        t0 = time.perf_counter()
+        L.lbm_init_fields(c3, rho_h, u_h)
+        L.lbm_step(c3, args.steps)
+        L.lbm_fields(c3, (n, n, n), rho=rho_o, u=u_o)
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0)
+        L.lbm_destroy(c3)
+        io_bytes = (rho.nbytes + u.nbytes)
+        e2e = {"value": world * cells * args.steps / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": io_bytes / args.steps, "d2h_bytes_per_step": io_bytes / args.steps,
+               "note": "lbm_init_fields(pinned host rho,u) + K x lbm_step + lbm_fields(pinned host rho,u)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": launch_s * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPE_NAME[prec], "data": "synthetic",
+                "config": workload_config(n, prec) | {"parallelism": f"replicas x{world}"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                             "kernel": f"fluid_step_kernel<{prec}>",
+                             "algorithmic_bytes_per_launch": algorithmic_bytes(n, prec)},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
+                "variants": variants}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_VALUE))
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D3Q19 central-moment lattice Boltzmann
+ * library (liblbm.so).
+ *
+ * Method: De Rosis & Coreixas, "Multiphysics flow simulations using D3Q19
+ * lattice Boltzmann methods based on central moments", arXiv:2010.01628.
+ * One time step streams the 19 populations (Eq. streaming), takes rho and u
+ * (Eq. macro, with +F/2 when a force acts, App. E), relaxes the central
+ * moments toward the Galilean-invariant equilibrium with the forcing terms
+ * (Eq. eq:posColl0 and the list after it), and rebuilds the populations by the
+ * two-step transform of App. C (Eqs. rawQ19, pdfQ19).  Physics modules add the
+ * Lorentz force with magnetic populations (Sec. III.F) or the colour-gradient
+ * two-phase operator (App. E).
+ *
+ * Conventions shared by every entry point:
+ *  - Lattice units (dx = dt = 1), c_s^2 = 1/3, omega = 1/(nu/c_s^2 + 1/2).
+ *  - Fields are FP64, layout [nz][ny][nx] with x fastest; vectors (u, B) are
+ *    three such planes back to back (x, y, z components).
+ *  - Field pointers may be host memory (pageable or pinned) or device memory
+ *    of the context's GPU; the library copies with cudaMemcpyAsync on the
+ *    context stream and synchronises before returning.
+ *  - The caller owns every pointer it passes in.  The library owns its device
+ *    buffers (populations, scratch), obtained from the allocator installed with
+ *    lbm_set_allocator, else cudaMalloc.
+ *  - Every call returns an lbm_status; nothing aborts or traps, and nothing
+ *    throws across the ABI.  lbm_last_error() gives a one-line reason.
+ *  - Kernels run asynchronously on the context stream.  lbm_step() returns
+ *    after enqueueing; errors of earlier launches surface at the next call
+ *    that synchronises (fields, reduce, sync, populations).
+ *  - Time-step order: the stored state is the post-collision populations; a
+ *    step gathers them (stream + boundaries) and collides.  The initial state
+ *    is the equilibrium of the given fields.  Reported fields are the moments
+ *    of the gathered (post-stream) populations.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument (sizes, rates, null pointers) */
+    LBM_ERR_OOM = 2,         /* device allocation failed */
+    LBM_ERR_CUDA = 3,        /* a CUDA call failed */
+    LBM_ERR_DIVERGED = 4,    /* NaN/Inf or rho <= 0 found by a reduction */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device wait (batch grid barrier) ran out */
+    LBM_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} lbm_status;
+
+typedef enum { LBM_D3Q19 = 0 } lbm_lattice;
+
+/* Population storage.  FP64 and FP32 store f_i - w_i (shifted by the rest
+ * equilibrium of rho0 = 1) and compute in their own type.  The 16-bit formats
+ * store (f_i - w_i)/w_i and compute in FP32 registers. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_SHIFTED = 2, LBM_BF16_SHIFTED = 3 } lbm_precision;
+
+typedef enum {
+    LBM_PHYS_FLUID = 0, /* single phase, body force F = rho g (Sec. II)           */
+    LBM_PHYS_MHD = 1,   /* + D3Q7 magnetic populations, F = j x b (Sec. III.F)    */
+    LBM_PHYS_CGM = 2    /* colour-gradient two-phase (App. E)                     */
+} lbm_physics;
+
+/* Box geometry.  A periodic axis wraps; a non-periodic axis has half-way
+ * bounce-back no-slip walls at both ends (the paper's regularized walls,
+ * Sec. III, are not implemented).  lid_u is the velocity of the +y wall
+ * (Ladd's moving-wall term with rho_w = 1); it is ignored if y is periodic. */
+typedef struct {
+    int nx, ny, nz;
+    unsigned periodic_mask; /* bit 0: x, bit 1: y, bit 2: z */
+    double lid_u[3];
+} lbm_grid;
+
+/* Diagonal relaxation matrix K of Sec. II.B: omega on the five deviatoric
+ * second-order CMs; omega_bulk on the trace (k4); omega_3 on k10..k15;
+ * omega_4 on k16..k18.  The paper sets omega_bulk = omega_3 = omega_4 = 1,
+ * the only values this build accepts (others give LBM_ERR_UNSUPPORTED). */
+typedef struct {
+    double omega, omega_bulk, omega_3, omega_4;
+} lbm_relax;
+
+/* Constant body acceleration: F = rho g (Sec. III.H, Eq. eq:posColl0). */
+typedef struct {
+    double g[3];
+} lbm_forcing;
+
+/* Physics-module parameters.
+ * MHD (Sec. III.F): tau_m is the relaxation time of the D3Q7 magnetic
+ *   populations (eta = (tau_m - 1/2)/4); b_wall is the field imposed at the
+ *   walls (anti-bounce-back).
+ * CGM (App. E): alpha_r, alpha_b set phi_i(alpha) and the density ratio
+ *   rho_r0/rho_b0 = (1 - alpha_b)/(1 - alpha_r); A is the perturbation
+ *   amplitude (sigma = (4/9) A / omega); beta the recolouring parameter. */
+typedef struct {
+    double tau_m;
+    double b_wall[3];
+    double alpha_r, alpha_b, A, beta;
+} lbm_physparams;
+
+/* Device-memory provider.  alloc returns a device pointer of at least `bytes`
+ * (256-byte aligned) usable on `stream`, or NULL; free releases it.  Passing
+ * NULL for both restores cudaMalloc/cudaFree.  Applies to contexts created
+ * afterwards; a context frees with the provider it allocated with. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_free_fn)(void *ptr, void *stream, void *user);
+lbm_status lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *user);
+
+/* Create a solver on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream); all work of the context is
+ * ordered on it.  grid sizes >= 1 with nx*ny*nz < 2^31; 0 < omega < 2.
+ * Populations start at rest (rho = 1, u = 0) until lbm_init_fields. */
+lbm_status lbm_create(lbm_ctx **out, const lbm_grid *grid, lbm_lattice lattice, const lbm_relax *relax,
+                      const lbm_forcing *forcing, lbm_physics physics, const lbm_physparams *phys,
+                      lbm_precision precision, void *cuda_stream);
+
+/* Set the populations to the equilibrium of the given fields (Sec. III
+ * opening paragraph: Eq. eq:EqQ19RM; App. E's h_eq for CGM; the magnetic
+ * equilibrium for MHD).  rho: [n]; u: [3n] or NULL (= 0); phase: [n], CGM
+ * only, the order parameter phi of Eq. eq:order; B: [3n], MHD only. */
+lbm_status lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u, const double *phase, const double *B);
+
+/* Enqueue n time steps on the context stream (n >= 0). */
+lbm_status lbm_step(lbm_ctx *ctx, long n);
+
+/* Macroscopic fields of the current state (any pointer may be NULL = skip):
+ * rho [n]; u [3n] (with +F/2); phase [n] (CGM); B [3n] (MHD).  Synchronises. */
+lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *phase, double *B);
+
+/* FP64 reductions over all nodes of the current state: total mass sum rho,
+ * total momentum sum rho u, and the residual ||u - u_prev||_2 / ||u||_2
+ * against the velocity recorded by the previous lbm_reduce call on this
+ * context (-1 on the first call).  Records u for the next call.  Returns
+ * LBM_ERR_DIVERGED if any node has a non-finite value or rho <= 0.  Any output
+ * pointer may be NULL.  Synchronises. */
+lbm_status lbm_reduce(lbm_ctx *ctx, double *out_mass, double *out_mom, double *out_residual);
+
+/* Steady-state driver: steps until the one-step residual (lbm_reduce's
+ * definition, evaluated every `check_every` steps) is <= tol, or until
+ * max_steps.  Reports the steps taken and the last residual. */
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, long max_steps, long check_every, double tol, long *steps_done,
+                             double *residual);
+
+/* Wait for all enqueued work; reports errors of earlier launches. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Raw population storage (checkpoint/restart).  Size in bytes of one copy of
+ * the state; the layout is the storage format (structure of arrays, planes of
+ * n values in direction order, the stored quantity as documented for
+ * lbm_precision; MHD appends 21 magnetic planes, CGM stores red then blue).
+ * dst/src may be host or device pointers. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes);
+
+void lbm_destroy(lbm_ctx *ctx);
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

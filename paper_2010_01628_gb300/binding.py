@@ -1,0 +1,274 @@
+"""ctypes binding of liblbm.so with the entry-point names of include/lbm.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device memory for the library comes from PyTorch's caching allocator (installed
+through ``lbm_set_allocator`` on first use) and work is ordered on PyTorch's
+current CUDA stream unless another stream is given.  If the library has not
+been built, importing this module raises; there is no CPU fallback.
+
+Field arrays are float64, layout [nz, ny, nx] (u, B: [3, nz, ny, nx]); they
+may be numpy arrays (host) or torch tensors (host, pinned or CUDA).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED = range(7)
+LBM_D3Q19 = 0
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+PHYSICS = {"fluid": 0, "mhd": 1, "cgm": 2}
+
+if not os.path.exists(_build.LIB):
+    raise ImportError(f"liblbm.so is not built ({_build.LIB}); run paper_2010_01628_gb300.build.build() first")
+
+_lib = ctypes.CDLL(_build.LIB)
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("periodic_mask", ctypes.c_uint),
+                ("lid_u", ctypes.c_double * 3)]
+
+
+class lbm_relax(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("omega_bulk", ctypes.c_double), ("omega_3", ctypes.c_double),
+                ("omega_4", ctypes.c_double)]
+
+
+class lbm_forcing(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double * 3)]
+
+
+class lbm_physparams(ctypes.Structure):
+    _fields_ = [("tau_m", ctypes.c_double), ("b_wall", ctypes.c_double * 3), ("alpha_r", ctypes.c_double),
+                ("alpha_b", ctypes.c_double), ("A", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_V = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_lib.lbm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, _V]
+_lib.lbm_create.argtypes = [ctypes.POINTER(_V), ctypes.POINTER(lbm_grid), ctypes.c_int, ctypes.POINTER(lbm_relax),
+                            ctypes.POINTER(lbm_forcing), ctypes.c_int, ctypes.POINTER(lbm_physparams), ctypes.c_int, _V]
+_lib.lbm_init_fields.argtypes = [_V, _V, _V, _V, _V]
+_lib.lbm_step.argtypes = [_V, ctypes.c_long]
+_lib.lbm_fields.argtypes = [_V, _V, _V, _V, _V]
+_lib.lbm_reduce.argtypes = [_V, _D, _D, _D]
+_lib.lbm_run_to_steady.argtypes = [_V, ctypes.c_long, ctypes.c_long, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_long), _D]
+_lib.lbm_sync.argtypes = [_V]
+_lib.lbm_state_bytes.argtypes = [_V]
+_lib.lbm_state_bytes.restype = ctypes.c_size_t
+_lib.lbm_get_populations.argtypes = [_V, _V, ctypes.c_size_t]
+_lib.lbm_set_populations.argtypes = [_V, _V, ctypes.c_size_t]
+_lib.lbm_destroy.argtypes = [_V]
+_lib.lbm_destroy.restype = None
+_lib.lbm_last_error.argtypes = [_V]
+_lib.lbm_last_error.restype = ctypes.c_char_p
+_lib.lbm_status_string.argtypes = [ctypes.c_int]
+_lib.lbm_status_string.restype = ctypes.c_char_p
+for _name in ("lbm_set_allocator", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_fields", "lbm_reduce",
+              "lbm_run_to_steady", "lbm_sync", "lbm_get_populations", "lbm_set_populations"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.lbm_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def _check(status, ctx=None):
+    if status != LBM_OK:
+        msg = _lib.lbm_last_error(ctx).decode() if ctx else ""
+        raise LBMError(status, msg)
+
+
+# --- device memory from PyTorch's caching allocator ------------------------------
+_alloc_refs = None
+
+
+def _torch():
+    try:
+        import torch
+        return torch if torch.cuda.is_available() else None
+    except ImportError:
+        return None
+
+
+def lbm_set_allocator(use_torch: bool = True) -> None:
+    """Install torch's caching allocator as the library's device-memory provider
+    (or restore cudaMalloc with use_torch=False)."""
+    global _alloc_refs
+    torch = _torch()
+    if not use_torch or torch is None:
+        _check(_lib.lbm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        _alloc_refs = None
+        return
+
+    def _alloc(size, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), torch.cuda.current_device(), int(stream or 0))
+        except Exception:  # the library reports LBM_ERR_OOM for a NULL
+            return None
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _alloc_refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(_lib.lbm_set_allocator(_alloc_refs[0], _alloc_refs[1], None))
+
+
+def _current_stream():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream if torch is not None else 0
+
+
+def _ptr(a, n_expected=None, writable=False):
+    """Raw pointer of a float64 C-contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("field arrays must be C-contiguous float64")
+        if writable and not a.flags["WRITEABLE"]:
+            raise TypeError("output array is read-only")
+        if n_expected is not None and a.size != n_expected:
+            raise ValueError(f"expected {n_expected} values, got {a.size}")
+        return a.ctypes.data
+    torch = __import__("torch")
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("field tensors must be contiguous float64")
+        if n_expected is not None and a.numel() != n_expected:
+            raise ValueError(f"expected {n_expected} values, got {a.numel()}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
+               physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0,
+               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
+    """Create a context; returns its handle (an int).  shape = (nx, ny, nz)."""
+    if _alloc_refs is None and _torch() is not None:
+        lbm_set_allocator(True)
+    gr = lbm_grid()
+    gr.nx, gr.ny, gr.nz = (int(v) for v in shape)
+    gr.periodic_mask = sum((1 << a) for a in range(3) if periodic[a])
+    for a in range(3):
+        gr.lid_u[a] = float(lid_u[a])
+    rl = lbm_relax(float(omega), float(omega_bulk), float(omega_3), float(omega_4))
+    fo = lbm_forcing()
+    for a in range(3):
+        fo.g[a] = float(g[a])
+    ph = lbm_physparams()
+    ph.tau_m = float(tau_m)
+    for a in range(3):
+        ph.b_wall[a] = float(b_wall[a])
+    ph.alpha_r, ph.alpha_b, ph.A, ph.beta = float(alpha_r), float(alpha_b), float(A), float(beta)
+    ctx = _V()
+    s = _current_stream() if stream is None else int(stream)
+    _check(_lib.lbm_create(ctypes.byref(ctx), ctypes.byref(gr), LBM_D3Q19, ctypes.byref(rl), ctypes.byref(fo),
+                           PHYSICS[physics], ctypes.byref(ph), PRECISIONS[precision], _V(s)))
+    return ctx.value
+
+
+def _n(ctx_shape):
+    nx, ny, nz = ctx_shape
+    return nx * ny * nz
+
+
+def lbm_init_fields(ctx, rho, u=None, phase=None, B=None):
+    n = int(np.prod(rho.shape))
+    _check(_lib.lbm_init_fields(ctx, _ptr(rho, n), _ptr(u, 3 * n), _ptr(phase, n), _ptr(B, 3 * n)), ctx)
+
+
+def lbm_step(ctx, n=1):
+    _check(_lib.lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_sync(ctx):
+    _check(_lib.lbm_sync(ctx), ctx)
+
+
+def lbm_fields(ctx, shape, rho=None, u=None, phase=None, B=None, want=("rho", "u")):
+    """Fill (or allocate on the host) the requested fields; returns a dict."""
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    out = {}
+    if rho is None and "rho" in want:
+        rho = np.empty((nz, ny, nx))
+    if u is None and "u" in want:
+        u = np.empty((3, nz, ny, nx))
+    if phase is None and "phase" in want:
+        phase = np.empty((nz, ny, nx))
+    if B is None and "B" in want:
+        B = np.empty((3, nz, ny, nx))
+    _check(_lib.lbm_fields(ctx, _ptr(rho, n, True), _ptr(u, 3 * n, True), _ptr(phase, n, True), _ptr(B, 3 * n, True)),
+           ctx)
+    for k, v in (("rho", rho), ("u", u), ("phase", phase), ("B", B)):
+        if v is not None:
+            out[k] = v
+    return out
+
+
+def lbm_reduce(ctx):
+    """(mass, momentum[3], residual) with lbm_reduce's semantics."""
+    m = ctypes.c_double()
+    mom = (ctypes.c_double * 3)()
+    r = ctypes.c_double()
+    _check(_lib.lbm_reduce(ctx, ctypes.byref(m), mom, ctypes.byref(r)), ctx)
+    return m.value, np.array(mom[:]), r.value
+
+
+def lbm_run_to_steady(ctx, max_steps, check_every=100, tol=1e-6):
+    steps = ctypes.c_long()
+    r = ctypes.c_double()
+    _check(_lib.lbm_run_to_steady(ctx, int(max_steps), int(check_every), float(tol), ctypes.byref(steps),
+                                  ctypes.byref(r)), ctx)
+    return steps.value, r.value
+
+
+def lbm_state_bytes(ctx):
+    return int(_lib.lbm_state_bytes(ctx))
+
+
+def lbm_get_populations(ctx, dst=None):
+    nb = lbm_state_bytes(ctx)
+    if dst is None:
+        dst = np.empty(nb, dtype=np.uint8)
+    ptr = dst.ctypes.data if isinstance(dst, np.ndarray) else dst.data_ptr()
+    _check(_lib.lbm_get_populations(ctx, _V(ptr), nb), ctx)
+    return dst
+
+
+def lbm_set_populations(ctx, src):
+    nb = lbm_state_bytes(ctx)
+    ptr = src.ctypes.data if isinstance(src, np.ndarray) else src.data_ptr()
+    size = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+    if size != nb:
+        raise ValueError(f"state is {nb} bytes, got {size}")
+    _check(_lib.lbm_set_populations(ctx, _V(ptr), nb), ctx)
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        _lib.lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx):
+    return _lib.lbm_last_error(ctx).decode()
+
+
+def lbm_status_string(status):
+    return _lib.lbm_status_string(int(status)).decode()
+
+
+def library_path() -> str:
+    return _build.LIB

@@ -1,0 +1,374 @@
+// lbm_cgm.cu -- colour-gradient two-phase step (App. E of arXiv:2010.01628).
+//
+// Two passes per step.  Pass 1 pulls the red and blue populations of every
+// node and writes the order parameter phi = (rho_r - rho_b)/(rho_r + rho_b)
+// (Eq. eq:order).  Pass 2 pulls them again, collides the total populations in
+// central-moment space toward h_eq (App. E post-collision list, with the 1/6 on
+// k16..18 that makes it reduce to rho c_s^4 at alpha = 1/3), adds the
+// surface-tension perturbation with the squared projection (c_i . grad phi)^2
+// (the mass-conserving form of Eq. eq:perturb), and recolours (Eqs. eq:op3r,
+// eq:op3b with g_eq(rho, 0) = rho phi_i(alpha)).  grad phi is the isotropic
+// stencil (1/c_s^2) sum_i w_i c_i phi(x + c_i); a neighbour behind a wall
+// contributes the node's own phi.
+//
+// Storage: planes 0..18 red, 19..37 blue, unshifted.
+#include "lbm_internal.h"
+#include "lbm_reduce.cuh"
+
+namespace lbm {
+
+struct CgmArgs {
+    Box box;
+    double omega, alpha_r, alpha_b, A, beta;
+    double g[3];
+};
+
+template <typename C>
+struct CgmNode {
+    C rho_r, rho_b, rho, ux, uy, uz, Fx, Fy, Fz, alpha;
+};
+
+template <typename C>
+__device__ __forceinline__ CgmNode<C> cgm_macro(const C (&fr)[Q], const C (&fb)[Q], C (&f)[Q], Moments<C>& m,
+                                                const CgmArgs& p) {
+    CgmNode<C> s;
+    C sr = (C)0, sb = (C)0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        sr += fr[i];
+        sb += fb[i];
+        f[i] = fr[i] + fb[i];
+    }
+    m = moments19(f);
+    s.rho_r = sr;
+    s.rho_b = sb;
+    s.rho = sr + sb;
+    s.Fx = s.rho * (C)p.g[0];
+    s.Fy = s.rho * (C)p.g[1];
+    s.Fz = s.rho * (C)p.g[2];
+    const C inv = (C)1 / s.rho;
+    s.ux = (m.jx + (C)0.5 * s.Fx) * inv;
+    s.uy = (m.jy + (C)0.5 * s.Fy) * inv;
+    s.uz = (m.jz + (C)0.5 * s.Fz) * inv;
+    s.alpha = (sr * (C)p.alpha_r + sb * (C)p.alpha_b) * inv;
+    return s;
+}
+
+// phi_i(alpha) of Eq. eq:varphi_ik.
+template <typename C, int I>
+__device__ __forceinline__ C cgm_phi_i(C alpha) {
+    constexpr int n2 = cx_of(I) * cx_of(I) + cy_of(I) * cy_of(I) + cz_of(I) * cz_of(I);
+    return n2 == 0 ? alpha : (n2 == 1 ? ((C)1 - alpha) * (C)(1.0 / 12.0) : ((C)1 - alpha) * (C)(1.0 / 24.0));
+}
+
+// Post-collision populations of the colour-gradient single-phase operator
+// (kd = (1 - omega) k5..9 computed from raw moments as in the single-phase
+// step; the equilibrated moments take App. E's values).
+template <typename C>
+__device__ __forceinline__ void cgm_collide(C (&f)[Q], const Moments<C>& m, const CgmNode<C>& s, C omega) {
+    const C rho = s.rho, ux = s.ux, uy = s.uy, uz = s.uz, al = s.alpha;
+    const C hx = (C)0.5 * s.Fx, hy = (C)0.5 * s.Fy, hz = (C)0.5 * s.Fz;
+    const C om1 = (C)1 - omega;
+    C kd[5];
+    kd[0] = om1 * (m.pxx_m_pyy - rho * (ux * ux - uy * uy) + (C)2 * (ux * hx - uy * hy));
+    kd[1] = om1 * (m.pyy_m_pzz - rho * (uy * uy - uz * uz) + (C)2 * (uy * hy - uz * hz));
+    kd[2] = om1 * (m.pxy - rho * ux * uy + ux * hy + uy * hx);
+    kd[3] = om1 * (m.pxz - rho * ux * uz + ux * hz + uz * hx);
+    kd[4] = om1 * (m.pyz - rho * uy * uz + uy * hz + uz * hy);
+    const C third = (C)(1.0 / 3.0);
+    const C a3 = rho * ((C)3 * al - (C)1) * (C)(1.0 / 6.0);
+    const C t[6] = {hy * third + a3 * uy, hx * third + a3 * ux, hz * third + a3 * uz,
+                    hx * third + a3 * ux, hz * third + a3 * uz, hy * third + a3 * uy};
+    const C k4 = (C)1.5 * rho * ((C)1 - al);
+    const C x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
+    const C sixth = (C)(1.0 / 6.0);
+    const C k16 = rho * ((C)1 + x2 + y2 - al * ((C)1 + (C)3 * x2 + (C)3 * y2)) * sixth;
+    const C k17 = rho * ((C)1 + x2 + z2 - al * ((C)1 + (C)3 * x2 + (C)3 * z2)) * sixth;
+    const C k18 = rho * ((C)1 + y2 + z2 - al * ((C)1 + (C)3 * y2 + (C)3 * z2)) * sixth;
+    back_transform<C>(rho, ux, uy, uz, hx, hy, hz, k4, rho, k4, kd, t, k16, k17, k18, f);
+}
+
+template <typename S, typename C, bool WALLS>
+__global__ void __launch_bounds__(256) cgm_phi_kernel(const S* __restrict__ src, C* __restrict__ phi, CgmArgs p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const Box& b = p.box;
+    if (x >= b.nx) return;
+    const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    const Nbr q = make_nbr(b, x, y, z);
+    C fr[Q], fb[Q];
+    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
+    gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
+    C sr = (C)0, sb = (C)0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        sr += fr[i];
+        sb += fb[i];
+    }
+    phi[self] = (sr - sb) / (sr + sb);
+}
+
+template <typename C, int I>
+__device__ __forceinline__ C phi_nbr(const C* __restrict__ phi, const Box& b, const Nbr& q, int x, int y, int z,
+                                     C own) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    const int sx = cx == 0 ? x : (cx > 0 ? q.xp : q.xm);
+    const int sy = cy == 0 ? y : (cy > 0 ? q.yp : q.ym);
+    const int sz = cz == 0 ? z : (cz > 0 ? q.zp : q.zm);
+    const bool wall = (cx > 0 && q.wxp) || (cx < 0 && q.wxm) || (cy > 0 && q.wyp) || (cy < 0 && q.wym) ||
+                      (cz > 0 && q.wzp) || (cz < 0 && q.wzm);
+    if (wall) return own;
+    return __ldg(phi + ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx);
+}
+
+template <typename C>
+__device__ __forceinline__ void grad_phi(const C* __restrict__ phi, const Box& b, const Nbr& q, int x, int y, int z,
+                                         uint32_t self, C (&gr)[3]) {
+    const C own = phi[self];
+    C gx = (C)0, gy = (C)0, gz = (C)0;
+#define LBM_GP(I)                                                            \
+    {                                                                        \
+        const C v = phi_nbr<C, I>(phi, b, q, x, y, z, own) * (C)w_of(I);     \
+        if (cx_of(I)) gx += (C)cx_of(I) * v;                                 \
+        if (cy_of(I)) gy += (C)cy_of(I) * v;                                 \
+        if (cz_of(I)) gz += (C)cz_of(I) * v;                                 \
+    }
+    LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9) LBM_GP(10)
+    LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
+#undef LBM_GP
+    gr[0] = (C)3 * gx;
+    gr[1] = (C)3 * gy;
+    gr[2] = (C)3 * gz;
+}
+
+template <typename S, typename C, int I>
+__device__ __forceinline__ void perturb_recolour_store(S* __restrict__ dst, size_t n, uint32_t self, C fi,
+                                                       const C (&gr)[3], C n2, C pert_amp, C inv_n2, C inv_nrm,
+                                                       C frac_r, C frac_b, C sep, C alpha) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    constexpr int c2 = cx * cx + cy * cy + cz * cz;
+    const C cg = (C)cx * gr[0] + (C)cy * gr[1] + (C)cz * gr[2];
+    if (n2 > (C)1e-24) {
+        const C Bi = c2 == 0 ? (C)(-1.0 / 3.0) : (c2 == 1 ? (C)(1.0 / 18.0) : (C)(1.0 / 36.0));
+        fi += pert_amp * ((C)w_of(I) * cg * cg * inv_n2 - Bi);
+    }
+    C cos_t = (C)0;
+    if (c2 > 0 && inv_nrm > (C)0) cos_t = cg * inv_nrm * (C)(c2 == 1 ? 1.0 : 0.70710678118654752440);
+    const C e = sep * cos_t * cgm_phi_i<C, I>(alpha);
+    Store<S>::store(dst + (size_t)I * n + self, frac_r * fi + e);
+    Store<S>::store(dst + (size_t)(Q + I) * n + self, frac_b * fi - e);
+}
+
+template <typename S, typename C, bool WALLS>
+__global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                          const C* __restrict__ phi, CgmArgs p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const Box& b = p.box;
+    if (x >= b.nx) return;
+    const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    const Nbr q = make_nbr(b, x, y, z);
+    C fr[Q], fb[Q], f[Q];
+    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
+    gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
+    Moments<C> m;
+    const CgmNode<C> s = cgm_macro<C>(fr, fb, f, m, p);
+    cgm_collide<C>(f, m, s, (C)p.omega);
+    C gr[3];
+    grad_phi<C>(phi, b, q, x, y, z, self, gr);
+    const C n2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+    const C nrm = sqrt(n2);
+    const C pert_amp = (C)0.5 * (C)p.A * nrm;
+    const C inv_n2 = n2 > (C)1e-24 ? (C)1 / n2 : (C)0;
+    const C inv_nrm = nrm > (C)1e-12 ? (C)1 / nrm : (C)0;
+    const C inv_rho = (C)1 / s.rho;
+    const C frac_r = s.rho_r * inv_rho, frac_b = s.rho_b * inv_rho;
+    // beta rho_r rho_b / rho^2 * g_eq(rho, 0) with g_eq = rho phi_i(alpha)
+    const C sep = (C)p.beta * s.rho_r * s.rho_b * inv_rho;
+#define LBM_PR(I) \
+    perturb_recolour_store<S, C, I>(dst, b.n, self, f[I], gr, n2, pert_amp, inv_n2, inv_nrm, frac_r, frac_b, sep, s.alpha);
+    LBM_PR(0) LBM_PR(1) LBM_PR(2) LBM_PR(3) LBM_PR(4) LBM_PR(5) LBM_PR(6) LBM_PR(7) LBM_PR(8) LBM_PR(9)
+    LBM_PR(10) LBM_PR(11) LBM_PR(12) LBM_PR(13) LBM_PR(14) LBM_PR(15) LBM_PR(16) LBM_PR(17) LBM_PR(18)
+#undef LBM_PR
+}
+
+template <typename S, typename C>
+__global__ void cgm_init_kernel(S* __restrict__ dst, const double* __restrict__ slab, CgmArgs p, int z0, int nzs,
+                                bool uniform) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, zs = blockIdx.z;
+    const Box& b = p.box;
+    if (x >= b.nx || zs >= nzs) return;
+    const size_t m = (size_t)b.nx * b.ny * nzs;
+    const size_t k = ((size_t)zs * b.ny + y) * b.nx + x;
+    const uint32_t self = ((uint32_t)(z0 + zs) * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    double rho = 1.0, ph = -1.0;
+    CgmNode<C> s;
+    s.ux = s.uy = s.uz = (C)0;
+    if (!uniform) {
+        rho = slab[k];
+        ph = slab[4 * m + k];
+        s.ux = (C)slab[m + k];
+        s.uy = (C)slab[2 * m + k];
+        s.uz = (C)slab[3 * m + k];
+    }
+    const double rr = rho * (1.0 + ph) * 0.5, rb = rho * (1.0 - ph) * 0.5;
+    s.rho_r = (C)rr;
+    s.rho_b = (C)rb;
+    s.rho = (C)rho;
+    s.Fx = s.Fy = s.Fz = (C)0;
+    s.alpha = (C)((rr * p.alpha_r + rb * p.alpha_b) / rho);
+    // h_eq = T^-1 k_eq: the CGM collision of a state with zero deviatoric CMs
+    Moments<C> mz;
+    mz.drho = mz.jx = mz.jy = mz.jz = (C)0;
+    const C r = s.rho;
+    mz.pxx_m_pyy = r * (s.ux * s.ux - s.uy * s.uy);
+    mz.pyy_m_pzz = r * (s.uy * s.uy - s.uz * s.uz);
+    mz.pxy = r * s.ux * s.uy;
+    mz.pxz = r * s.ux * s.uz;
+    mz.pyz = r * s.uy * s.uz;
+    C h[Q];
+    cgm_collide<C>(h, mz, s, (C)0);  // omega = 0 keeps kd = k5..9 = 0 exactly
+    const C fr = (C)(rr / rho), fbl = (C)(rb / rho);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        Store<S>::store(dst + (size_t)i * b.n + self, fr * h[i]);
+        Store<S>::store(dst + (size_t)(Q + i) * b.n + self, fbl * h[i]);
+    }
+}
+
+template <typename S, typename C, bool WALLS>
+__global__ void cgm_fields_kernel(const S* __restrict__ src, double* __restrict__ slab, CgmArgs p, int z0, int nzs) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, zs = blockIdx.z;
+    const Box& b = p.box;
+    if (x >= b.nx || zs >= nzs) return;
+    const int z = z0 + zs;
+    const size_t m = (size_t)b.nx * b.ny * nzs;
+    const size_t k = ((size_t)zs * b.ny + y) * b.nx + x;
+    const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    const Nbr q = make_nbr(b, x, y, z);
+    C fr[Q], fb[Q], f[Q];
+    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
+    gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
+    Moments<C> mo;
+    const CgmNode<C> s = cgm_macro<C>(fr, fb, f, mo, p);
+    slab[k] = (double)s.rho;
+    slab[m + k] = (double)s.ux;
+    slab[2 * m + k] = (double)s.uy;
+    slab[3 * m + k] = (double)s.uz;
+    slab[4 * m + k] = (double)((s.rho_r - s.rho_b) / s.rho);
+}
+
+template <typename S, typename C, bool WALLS>
+__global__ void __launch_bounds__(RED_THREADS) cgm_reduce_kernel(const S* __restrict__ src, CgmArgs p,
+                                                                 C* __restrict__ uprev, bool have_prev, bool record,
+                                                                 double* __restrict__ partials) {
+    const Box& b = p.box;
+    const int chunks_x = (b.nx + RED_THREADS - 1) / RED_THREADS;
+    const long total = (long)chunks_x * b.ny * b.nz;
+    RedAcc acc;
+    acc.zero();
+    for (long ch = blockIdx.x; ch < total; ch += gridDim.x) {
+        const int cxk = (int)(ch % chunks_x);
+        const long row = ch / chunks_x;
+        const int y = (int)(row % b.ny), z = (int)(row / b.ny);
+        const int x = cxk * RED_THREADS + threadIdx.x;
+        if (x < b.nx) {
+            const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+            const Nbr q = make_nbr(b, x, y, z);
+            C fr[Q], fb[Q], f[Q];
+            gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
+            gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
+            Moments<C> mo;
+            const CgmNode<C> s = cgm_macro<C>(fr, fb, f, mo, p);
+            reduce_node<C>(acc, s.rho, s.ux, s.uy, s.uz, uprev, b.n, self, have_prev, record);
+        }
+    }
+    block_reduce_store(acc, partials);
+}
+
+// ---------------------------------------------------------------------------
+static CgmArgs cgm_args(const lbm_ctx* c) {
+    CgmArgs p;
+    p.box = c->box;
+    p.omega = c->relax.omega;
+    p.alpha_r = c->phys.alpha_r;
+    p.alpha_b = c->phys.alpha_b;
+    p.A = c->phys.A;
+    p.beta = c->phys.beta;
+    for (int a = 0; a < 3; ++a) p.g[a] = c->forcing.g[a];
+    return p;
+}
+
+template <typename S, typename C>
+static cudaError_t step_t(lbm_ctx* c, long n) {
+    const CgmArgs p = cgm_args(c);
+    const bool walls = (c->box.periodic & 7u) != 7u;
+    const int bx = c->block_x;
+    const dim3 grid = step_grid(c->box, bx);
+    C* phi = (C*)c->phi;
+    for (long s = 0; s < n; ++s) {
+        const S* src = (const S*)c->buf[c->cur];
+        S* dst = (S*)c->buf[c->cur ^ 1];
+        if (walls) {
+            cgm_phi_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, phi, p);
+            cgm_collide_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, dst, phi, p);
+        } else {
+            cgm_phi_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, phi, p);
+            cgm_collide_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, dst, phi, p);
+        }
+        c->cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+static cudaError_t init_t(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform) {
+    const int bx = c->block_x;
+    dim3 grid((unsigned)((c->box.nx + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)nzs);
+    cgm_init_kernel<S, C><<<grid, bx, 0, c->stream>>>((S*)c->buf[c->cur], slab, cgm_args(c), z0, nzs, uniform);
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+static cudaError_t fields_t(lbm_ctx* c, double* slab, int z0, int nzs) {
+    const CgmArgs p = cgm_args(c);
+    const int bx = c->block_x;
+    dim3 grid((unsigned)((c->box.nx + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)nzs);
+    if ((c->box.periodic & 7u) != 7u)
+        cgm_fields_kernel<S, C, true><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], slab, p, z0, nzs);
+    else
+        cgm_fields_kernel<S, C, false><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], slab, p, z0, nzs);
+    return cudaGetLastError();
+}
+
+template <typename S, typename C>
+static cudaError_t reduce_t(lbm_ctx* c, bool record) {
+    const CgmArgs p = cgm_args(c);
+    if ((c->box.periodic & 7u) != 7u)
+        cgm_reduce_kernel<S, C, true><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
+            (const S*)c->buf[c->cur], p, (C*)c->uprev, c->have_prev, record, c->partials);
+    else
+        cgm_reduce_kernel<S, C, false><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
+            (const S*)c->buf[c->cur], p, (C*)c->uprev, c->have_prev, record, c->partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return reduce_finalize(c);
+}
+
+cudaError_t cgm_step(lbm_ctx* c, long n) {
+    return c->prec == LBM_FP64 ? step_t<double, double>(c, n) : step_t<float, float>(c, n);
+}
+cudaError_t cgm_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform) {
+    return c->prec == LBM_FP64 ? init_t<double, double>(c, slab, z0, nzs, uniform)
+                               : init_t<float, float>(c, slab, z0, nzs, uniform);
+}
+cudaError_t cgm_fields(lbm_ctx* c, double* slab, int z0, int nzs) {
+    return c->prec == LBM_FP64 ? fields_t<double, double>(c, slab, z0, nzs) : fields_t<float, float>(c, slab, z0, nzs);
+}
+cudaError_t cgm_reduce(lbm_ctx* c, bool record) {
+    return c->prec == LBM_FP64 ? reduce_t<double, double>(c, record) : reduce_t<float, float>(c, record);
+}
+
+}  // namespace lbm

@@ -1,0 +1,305 @@
+// lbm_device.cuh -- device-side building blocks of the D3Q19 central-moment
+// LBM step (arXiv:2010.01628): lattice tables, storage formats, the gather
+// (streaming + boundaries) and the collision in central-moment space.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// D3Q19 lattice in the paper's direction order (Sec. II.A): opposite(i) = i+9
+// for i = 1..9.  Weights 1/3 (rest), 1/18 (axes), 1/36 (face diagonals).
+__host__ __device__ constexpr int cx_of(int i) {
+    constexpr int t[19] = {0, -1, 0, 0, -1, -1, -1, -1, 0, 0, 1, 0, 0, 1, 1, 1, 1, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int cy_of(int i) {
+    constexpr int t[19] = {0, 0, -1, 0, -1, 1, 0, 0, -1, -1, 0, 1, 0, 1, -1, 0, 0, 1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int cz_of(int i) {
+    constexpr int t[19] = {0, 0, 0, -1, 0, 0, -1, 1, -1, 1, 0, 0, 1, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+__host__ __device__ constexpr double w_of(int i) {
+    return i == 0 ? 1.0 / 3.0
+                  : ((cx_of(i) * cx_of(i) + cy_of(i) * cy_of(i) + cz_of(i) * cz_of(i)) == 1 ? 1.0 / 18.0
+                                                                                          : 1.0 / 36.0);
+}
+
+constexpr int Q = 19;
+
+// Box boundary description used by every kernel.
+struct Box {
+    int nx, ny, nz;
+    unsigned periodic;  // bit 0 x, bit 1 y, bit 2 z
+    size_t n;           // nx*ny*nz (plane stride)
+};
+
+// ---------------------------------------------------------------------------
+// Storage formats.  FP64/FP32 hold f - w (shift by the rest state of rho0 = 1);
+// the 16-bit formats hold (f - w)/w so every direction uses the same range.
+template <typename S> struct Store;
+template <> struct Store<double> {
+    static constexpr bool scaled = false;
+    __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
+    __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
+};
+template <> struct Store<float> {
+    static constexpr bool scaled = false;
+    __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
+    __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
+};
+template <> struct Store<__half> {
+    static constexpr bool scaled = true;
+    __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static constexpr bool scaled = true;
+    __device__ static __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Read the shifted population f - w of direction I from storage.
+template <typename S, typename C, int I>
+__device__ __forceinline__ C load_shifted(const S* p) {
+    C v = (C)Store<S>::load(p);
+    if (Store<S>::scaled) v *= (C)w_of(I);
+    return v;
+}
+template <typename S, typename C, int I>
+__device__ __forceinline__ void store_shifted(S* p, C v) {
+    if (Store<S>::scaled) v *= (C)(1.0 / w_of(I));
+    Store<S>::store(p, v);
+}
+
+// ---------------------------------------------------------------------------
+// Neighbourhood of one node: wrapped neighbour coordinates along each axis and
+// whether stepping off the node in that direction leaves the box through a
+// wall (half-way bounce-back).
+struct Nbr {
+    int xm, xp, ym, yp, zm, zp;    // x-1, x+1, ... wrapped (valid only if not a wall)
+    bool wxm, wxp, wym, wyp, wzm, wzp;
+};
+
+__device__ __forceinline__ Nbr make_nbr(const Box& b, int x, int y, int z) {
+    Nbr q;
+    const bool px = b.periodic & 1u, py = b.periodic & 2u, pz = b.periodic & 4u;
+    q.xm = x == 0 ? b.nx - 1 : x - 1;
+    q.xp = x == b.nx - 1 ? 0 : x + 1;
+    q.ym = y == 0 ? b.ny - 1 : y - 1;
+    q.yp = y == b.ny - 1 ? 0 : y + 1;
+    q.zm = z == 0 ? b.nz - 1 : z - 1;
+    q.zp = z == b.nz - 1 ? 0 : z + 1;
+    q.wxm = !px && x == 0;
+    q.wxp = !px && x == b.nx - 1;
+    q.wym = !py && y == 0;
+    q.wyp = !py && y == b.ny - 1;
+    q.wzm = !pz && z == 0;
+    q.wzp = !pz && z == b.nz - 1;
+    return q;
+}
+
+// Source node of the pull x - c_i and whether it lies behind a wall.
+template <int I>
+__device__ __forceinline__ bool pull_source(const Box& b, const Nbr& q, int x, int y, int z, uint32_t& cell) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    const int sx = cx == 0 ? x : (cx > 0 ? q.xm : q.xp);
+    const int sy = cy == 0 ? y : (cy > 0 ? q.ym : q.yp);
+    const int sz = cz == 0 ? z : (cz > 0 ? q.zm : q.zp);
+    const bool wall = (cx > 0 && q.wxm) || (cx < 0 && q.wxp) || (cy > 0 && q.wym) || (cy < 0 && q.wyp) ||
+                      (cz > 0 && q.wzm) || (cz < 0 && q.wzp);
+    cell = ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx;
+    return wall;
+}
+
+// One pulled population f_I(x) = f*_I(x - c_I) (shifted).
+template <typename S, typename C, bool WALLS, int I>
+__device__ __forceinline__ C gather_one(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
+                                        uint32_t self, C lx, C ly, C lz) {
+    uint32_t cell;
+    const bool wall = pull_source<I>(b, q, x, y, z, cell);
+    if (!WALLS || !wall) return load_shifted<S, C, I>(src + (size_t)I * b.n + cell);
+    C v = load_shifted<S, C, opp_of(I)>(src + (size_t)opp_of(I) * b.n + self);
+    if (cy_of(I) < 0 && q.wyp)  // source beyond the +y face: the moving lid
+        v += (C)(6.0 * w_of(I)) * ((C)cx_of(I) * lx + (C)cy_of(I) * ly + (C)cz_of(I) * lz);
+    return v;
+}
+
+// Gather of the 19 shifted populations (Eq. streaming in pull form).  WALLS
+// selects the variant with bounce-back; a pull from behind a wall reads the
+// node's own post-collision population of the opposite direction, plus
+// 6 w_i c_i . u_lid when the wall crossed is the moving +y lid.
+template <typename S, typename C, bool WALLS>
+__device__ __forceinline__ void gather19(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
+                                         uint32_t self, C lx, C ly, C lz, C (&f)[Q]) {
+#define LBM_G(I) f[I] = gather_one<S, C, WALLS, I>(src, b, q, x, y, z, self, lx, ly, lz);
+    LBM_G(0) LBM_G(1) LBM_G(2) LBM_G(3) LBM_G(4) LBM_G(5) LBM_G(6) LBM_G(7) LBM_G(8) LBM_G(9) LBM_G(10)
+    LBM_G(11) LBM_G(12) LBM_G(13) LBM_G(14) LBM_G(15) LBM_G(16) LBM_G(17) LBM_G(18)
+#undef LBM_G
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ void scatter19(S* __restrict__ dst, size_t n, uint32_t self, const C (&f)[Q]) {
+#define LBM_STORE(I) store_shifted<S, C, I>(dst + (size_t)I * n + self, f[I]);
+    LBM_STORE(0) LBM_STORE(1) LBM_STORE(2) LBM_STORE(3) LBM_STORE(4) LBM_STORE(5) LBM_STORE(6) LBM_STORE(7)
+    LBM_STORE(8) LBM_STORE(9) LBM_STORE(10) LBM_STORE(11) LBM_STORE(12) LBM_STORE(13) LBM_STORE(14)
+    LBM_STORE(15) LBM_STORE(16) LBM_STORE(17) LBM_STORE(18)
+#undef LBM_STORE
+}
+
+// ---------------------------------------------------------------------------
+// Raw moments of the shifted populations: d = sum (f - w) = rho - 1, the
+// momentum j = sum f c, and the shifted second moments (the w parts of
+// sum f c_a c_b cancel in every combination used below).
+template <typename C>
+struct Moments {
+    C drho, jx, jy, jz;
+    C pxx_m_pyy, pyy_m_pzz, pxy, pxz, pyz;
+};
+
+template <typename C>
+__device__ __forceinline__ Moments<C> moments19(const C (&f)[Q]) {
+    Moments<C> m;
+    const C sx_p = f[10] + f[13] + f[14] + f[15] + f[16];  // c_x = +1
+    const C sx_m = f[1] + f[4] + f[5] + f[6] + f[7];       // c_x = -1
+    const C sy_p = f[5] + f[11] + f[13] + f[17] + f[18];
+    const C sy_m = f[2] + f[4] + f[8] + f[9] + f[14];
+    const C sz_p = f[7] + f[9] + f[12] + f[15] + f[17];
+    const C sz_m = f[3] + f[6] + f[8] + f[16] + f[18];
+    m.jx = sx_p - sx_m;
+    m.jy = sy_p - sy_m;
+    m.jz = sz_p - sz_m;
+    // sum_i f c_a^2: directions with c_a != 0 are exactly those counted above
+    const C pxx = sx_p + sx_m, pyy = sy_p + sy_m, pzz = sz_p + sz_m;
+    m.drho = f[0] + (f[1] + f[10]) + (f[2] + f[11]) + (f[3] + f[12]) + (f[4] + f[13]) + (f[5] + f[14]) +
+             (f[6] + f[15]) + (f[7] + f[16]) + (f[8] + f[17]) + (f[9] + f[18]);
+    m.pxx_m_pyy = pxx - pyy;
+    m.pyy_m_pzz = pyy - pzz;
+    m.pxy = (f[4] + f[13]) - (f[5] + f[14]);
+    m.pxz = (f[6] + f[15]) - (f[7] + f[16]);
+    m.pyz = (f[8] + f[17]) - (f[9] + f[18]);
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Back-transform of App. C in two steps, r* = N^-1 k* (Eq. rawQ19) then
+// f* = M^-1 r* (Eq. pdfQ19), for a post-collision CM vector with
+//   k1..3 = h (= F/2), k4 (enters the products with u), k5..9 = kd[0..4],
+//   k10..15 = t[0..5], and the "standalone" parts r0c (of r0), k4c (of r4),
+//   k16c..18c (of r16..18).
+// With r0c = rho - 1, k4c = k4 - 1 and k16c = k16 - 1/9 the result is
+// f* - w directly (M^-1 maps (1,0,0,0,1,0..0,1/9,1/9,1/9) to w), so shifted
+// storage loses no digits to the O(1) rest state.  The c_s^2 factors on the
+// k5/k6 terms of r16..18 follow from the expansion c = cbar + u.
+template <typename C>
+__device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C hy, C hz, C k4, C r0c, C k4c,
+                                               const C (&kd)[5], const C (&t)[6], C k16c, C k17c, C k18c,
+                                               C (&f)[Q]) {
+    const C third = (C)(1.0 / 3.0);
+    const C x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
+    const C k5 = kd[0], k6 = kd[1], k7 = kd[2], k8 = kd[3], k9 = kd[4];
+    // sum f cbar_x^2 etc. expressed through k4, k5, k6 (times c_s^2 = 1/3)
+    const C Xs = (k4 + (C)2 * k5 + k6) * third;  // sum f cbar_x^2
+    const C Ys = (k4 - k5 + k6) * third;         // sum f cbar_y^2
+    const C Zs = (k4 - k5 - (C)2 * k6) * third;  // sum f cbar_z^2
+
+    C r[Q];
+    r[0] = r0c;
+    r[1] = rho * ux + hx;
+    r[2] = rho * uy + hy;
+    r[3] = rho * uz + hz;
+    r[4] = rho * (x2 + y2 + z2) + (C)2 * (ux * hx + uy * hy + uz * hz) + k4c;
+    r[5] = rho * (x2 - y2) + (C)2 * (ux * hx - uy * hy) + k5;
+    r[6] = rho * (y2 - z2) + (C)2 * (uy * hy - uz * hz) + k6;
+    r[7] = rho * ux * uy + uy * hx + ux * hy + k7;
+    r[8] = rho * ux * uz + uz * hx + ux * hz + k8;
+    r[9] = rho * uy * uz + uz * hy + uy * hz + k9;
+    // third order: sum f c_a^2 c_b = k(a^2 b) + u_b Xa + 2 u_a k(ab) + 2 u_a u_b h_a + u_a^2 h_b + rho u_a^2 u_b
+    r[10] = rho * x2 * uy + (C)2 * ux * uy * hx + x2 * hy + uy * Xs + (C)2 * ux * k7 + t[0];
+    r[11] = rho * ux * y2 + y2 * hx + (C)2 * ux * uy * hy + ux * Ys + (C)2 * uy * k7 + t[1];
+    r[12] = rho * x2 * uz + (C)2 * ux * uz * hx + x2 * hz + uz * Xs + (C)2 * ux * k8 + t[2];
+    r[13] = rho * ux * z2 + z2 * hx + (C)2 * ux * uz * hz + ux * Zs + (C)2 * uz * k8 + t[3];
+    r[14] = rho * y2 * uz + (C)2 * uy * uz * hy + y2 * hz + uz * Ys + (C)2 * uy * k9 + t[4];
+    r[15] = rho * uy * z2 + z2 * hy + (C)2 * uy * uz * hz + uy * Zs + (C)2 * uz * k9 + t[5];
+    // fourth order: sum f c_a^2 c_b^2
+    r[16] = rho * x2 * y2 + (C)2 * ux * y2 * hx + (C)2 * x2 * uy * hy + y2 * Xs + x2 * Ys + (C)4 * ux * uy * k7 +
+            (C)2 * uy * t[0] + (C)2 * ux * t[1] + k16c;
+    r[17] = rho * x2 * z2 + (C)2 * ux * z2 * hx + (C)2 * x2 * uz * hz + z2 * Xs + x2 * Zs + (C)4 * ux * uz * k8 +
+            (C)2 * uz * t[2] + (C)2 * ux * t[3] + k17c;
+    r[18] = rho * y2 * z2 + (C)2 * uy * z2 * hy + (C)2 * y2 * uz * hz + z2 * Ys + y2 * Zs + (C)4 * uy * uz * k9 +
+            (C)2 * uz * t[4] + (C)2 * uy * t[5] + k18c;
+
+    const C half = (C)0.5, quarter = (C)0.25, sixth = (C)(1.0 / 6.0);
+    const C ax = (r[4] + (C)2 * r[5] + r[6]) * sixth;
+    const C ay = (r[4] - r[5] + r[6]) * sixth;
+    const C az = (r[4] - r[5] - (C)2 * r[6]) * sixth;
+    const C s1617 = r[16] + r[17], s1618 = r[16] + r[18], s1718 = r[17] + r[18];
+    f[0] = r[0] - r[4] + r[16] + s1718;
+    const C bx = (r[11] + r[13]) * half, by = (r[10] + r[15]) * half, bz = (r[12] + r[14]) * half;
+    f[1] = bx - (r[1] + s1617) * half + ax;
+    f[10] = -bx + (r[1] - s1617) * half + ax;
+    f[2] = by - (r[2] + s1618) * half + ay;
+    f[11] = -by + (r[2] - s1618) * half + ay;
+    f[3] = bz - (r[3] + s1718) * half + az;
+    f[12] = -bz + (r[3] - s1718) * half + az;
+    f[4] = (r[7] + r[16] - r[10] - r[11]) * quarter;
+    f[5] = (r[10] + r[16] - r[7] - r[11]) * quarter;
+    f[13] = (r[7] + r[10] + r[11] + r[16]) * quarter;
+    f[14] = (r[11] + r[16] - r[7] - r[10]) * quarter;
+    f[6] = (r[8] + r[17] - r[12] - r[13]) * quarter;
+    f[7] = (r[12] + r[17] - r[8] - r[13]) * quarter;
+    f[15] = (r[8] + r[12] + r[13] + r[17]) * quarter;
+    f[16] = (r[13] + r[17] - r[8] - r[12]) * quarter;
+    f[8] = (r[9] + r[18] - r[14] - r[15]) * quarter;
+    f[9] = (r[14] + r[18] - r[9] - r[15]) * quarter;
+    f[17] = (r[9] + r[14] + r[15] + r[18]) * quarter;
+    f[18] = (r[15] + r[18] - r[9] - r[14]) * quarter;
+}
+
+// Macroscopic state of a gathered node: rho, F, u = (sum f c + F/2)/rho.
+template <typename C>
+struct Macro {
+    C rho, ux, uy, uz, Fx, Fy, Fz;
+};
+
+// Single-phase forced CM collision (Sec. II.B, list after Eq. eq:posColl0),
+// in shifted variables: f holds f - w on entry and f* - w on exit.
+template <typename C>
+__device__ __forceinline__ void collide_fluid(C (&f)[Q], const Moments<C>& m, const Macro<C>& a, C omega) {
+    const C rho = a.rho, ux = a.ux, uy = a.uy, uz = a.uz;
+    const C hx = (C)0.5 * a.Fx, hy = (C)0.5 * a.Fy, hz = (C)0.5 * a.Fz;
+    const C om1 = (C)1 - omega;
+    // pre-collision central second moments (Eq. pre_collision_central_moments)
+    // from raw moments: sum f cbar_a cbar_b = P_ab - rho u_a u_b + (u_a F_b + u_b F_a)/2
+    C kd[5];
+    kd[0] = om1 * (m.pxx_m_pyy - rho * (ux * ux - uy * uy) + (C)2 * (ux * hx - uy * hy));
+    kd[1] = om1 * (m.pyy_m_pzz - rho * (uy * uy - uz * uz) + (C)2 * (uy * hy - uz * hz));
+    kd[2] = om1 * (m.pxy - rho * ux * uy + ux * hy + uy * hx);
+    kd[3] = om1 * (m.pxz - rho * ux * uz + ux * hz + uz * hx);
+    kd[4] = om1 * (m.pyz - rho * uy * uz + uy * hz + uz * hy);
+    const C third = (C)(1.0 / 3.0);
+    // k10..15* = c_s^2 F/2 in the order (Fy, Fx, Fz, Fx, Fz, Fy)
+    const C t[6] = {hy * third, hx * third, hz * third, hx * third, hz * third, hy * third};
+    const C drho = m.drho;
+    const C k16c = drho * (C)(1.0 / 9.0);
+    back_transform<C>(rho, ux, uy, uz, hx, hy, hz, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+}
+
+// Equilibrium of (rho, u) in shifted form: the back-transform of k_eq.
+template <typename C>
+__device__ __forceinline__ void equilibrium_shifted(C rho, C drho, C ux, C uy, C uz, C (&f)[Q]) {
+    const C z = (C)0;
+    const C kd[5] = {z, z, z, z, z};
+    const C t[6] = {z, z, z, z, z, z};
+    const C k16c = drho * (C)(1.0 / 9.0);
+    back_transform<C>(rho, ux, uy, uz, z, z, z, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+}
+
+}  // namespace lbm
