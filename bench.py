@@ -62,7 +62,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def committed_traffic(kernel_key):
+def committed_traffic(kernel_key, group="fluid"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (matched by hash); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -74,7 +74,7 @@ def committed_traffic(kernel_key):
         return None
     try:
         from paper_2010_01628_gb300 import build
-        if ent.get("source_sha") != build.source_hash():
+        if ent.get("source_sha") != build.source_hash(group):
             return None
     except Exception:
         return None

@@ -37,11 +37,21 @@ def _deps():
         os.path.join(HERE, "..", "include", "lbm.h")]
 
 
-def source_hash() -> str:
-    """SHA-256 over the library sources (identifies the kernels a profile was taken on)."""
+# Device sources that determine each kernel family's machine code.
+KERNEL_SOURCES = {
+    "fluid": ["lbm_device.cuh", "lbm_fluid.cu"],
+    "mhd": ["lbm_device.cuh", "lbm_mhd.cu"],
+    "cgm": ["lbm_device.cuh", "lbm_cgm.cu"],
+}
+
+
+def source_hash(group: str | None = None) -> str:
+    """SHA-256 over the library sources, or over one kernel family's device
+    sources (identifies the kernels a profile was taken on)."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(_deps()):
+    files = _deps() if group is None else [os.path.join(CSRC, f) for f in KERNEL_SOURCES[group]]
+    for p in sorted(files):
         h.update(os.path.basename(p).encode())
         with open(p, "rb") as fh:
             h.update(fh.read())

@@ -12,6 +12,13 @@
 
 namespace lbm {
 
+struct FluidArgs {
+    Box box;
+    double omega;
+    double g[3];
+    double lid[3];
+};
+
 template <typename C>
 __device__ __forceinline__ Macro<C> fluid_macro(const Moments<C>& m, C gx, C gy, C gz) {
     Macro<C> a;

@@ -45,13 +45,6 @@ constexpr int RED_WIDTH = 8;  // mass, mom x/y/z, |du|^2, |u|^2, bad-node count,
 constexpr int RED_BLOCKS = 1216;  // 152 SMs x 8
 constexpr int RED_THREADS = 256;
 
-struct FluidArgs {
-    Box box;
-    double omega;
-    double g[3];
-    double lid[3];
-};
-
 // Kernel launchers, one per physics module; each returns cudaGetLastError().
 cudaError_t fluid_step(lbm_ctx* c, long n);
 cudaError_t fluid_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
