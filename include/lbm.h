@@ -157,6 +157,29 @@ size_t lbm_state_bytes(const lbm_ctx *ctx);
 lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes);
 
+/* Allocation-free FP64 reduction of a single-phase population state that the
+ * caller owns (the paper has no counterpart; it exists for callers that may
+ * not allocate device memory: applications that own all device memory
+ * through their own pool, latency-critical loops where cudaMalloc/cudaFree
+ * would stall, code running inside an allocator or memory-pressure callback).
+ * populations: device pointer to one state in the storage format of
+ *   lbm_get_populations for LBM_PHYS_FLUID with this precision (19 planes).
+ * grid, forcing: as for lbm_create (forcing may be NULL = no force).
+ * out: device-accessible pointer to 5 doubles, written with the sums over all
+ *   nodes of rho, rho u (x, y, z; with +F/2) and the number of nodes with a
+ *   non-finite value or rho <= 0, the same quantities lbm_reduce reports.
+ * The work is enqueued on cuda_stream; the call does not synchronise.
+ * It allocates nothing: its scratch is a fixed 77,824-byte __device__ array
+ * (1216 block partials) that every GPU loading the library holds until exit.
+ * Grids beyond 2^31 - 1 nodes, or with ny or nz above 65535, are rejected with
+ * LBM_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * err/err_len (optional) receive a one-line reason on failure. */
+lbm_status lbm_reduce_state_noalloc(const void *populations, lbm_precision precision, const lbm_grid *grid,
+                                    const lbm_forcing *forcing, double *out, void *cuda_stream, char *err,
+                                    size_t err_len);
+
 void lbm_destroy(lbm_ctx *ctx);
 const char *lbm_last_error(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);

@@ -257,6 +257,31 @@ def lbm_set_populations(ctx, src):
     _check(_lib.lbm_set_populations(ctx, _V(ptr), nb), ctx)
 
 
+_lib.lbm_reduce_state_noalloc.argtypes = [_V, ctypes.c_int, ctypes.POINTER(lbm_grid), ctypes.POINTER(lbm_forcing),
+                                          _V, _V, ctypes.c_char_p, ctypes.c_size_t]
+_lib.lbm_reduce_state_noalloc.restype = ctypes.c_int
+
+
+def lbm_reduce_state_noalloc(populations, shape, out, *, precision="fp32", periodic=(True, True, True),
+                             lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), stream=None):
+    """Allocation-free reduction of a caller-owned state.  populations and out
+    are CUDA tensors (out: 5 float64).  Enqueued on the stream, not synchronised."""
+    gr = lbm_grid()
+    gr.nx, gr.ny, gr.nz = (int(v) for v in shape)
+    gr.periodic_mask = sum((1 << a) for a in range(3) if periodic[a])
+    for a in range(3):
+        gr.lid_u[a] = float(lid_u[a])
+    fo = lbm_forcing()
+    for a in range(3):
+        fo.g[a] = float(g[a])
+    err = ctypes.create_string_buffer(256)
+    s = _current_stream() if stream is None else int(stream)
+    status = _lib.lbm_reduce_state_noalloc(_V(populations.data_ptr()), PRECISIONS[precision], ctypes.byref(gr),
+                                           ctypes.byref(fo), _V(out.data_ptr()), _V(s), err, 256)
+    if status != LBM_OK:
+        raise LBMError(status, err.value.decode())
+
+
 def lbm_destroy(ctx):
     if ctx:
         _lib.lbm_destroy(ctx)
