@@ -204,6 +204,100 @@ def run_reference(args):
     return 0
 
 
+def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=256):
+    """Throughput of the other configurations of the method, each with its own
+    algorithmic bytes per lattice update (populations read + written plus the
+    coupled fields).  ``only`` restricts the run to one of them (profiling)."""
+    out = {}
+
+    def timed(fn, n):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(n)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    if only in (None, "tg32"):
+        out.update(_tg32(L, timed))
+    if only in (None, "mhd_batch"):
+        out.update(_mhd_batch(L, timed, steps, peak, domains))
+    if only in (None, "cgm"):
+        out.update(_cgm(L, timed, steps, peak, n_cgm))
+    return out
+
+
+def _tg32(L, timed):
+    # C1: 3D Taylor-Green vortex 32^3, FP64, 200 steps (launch-bound size).
+    out = {}
+    rho, u = inputs.taylor_green_3d(32, u0=0.05)
+    c = L.lbm_create((32, 32, 32), 1 / 0.53, precision="fp64")
+    L.lbm_init_fields(c, rho, u)
+    L.lbm_step(c, 5)
+    t = timed(lambda n: L.lbm_step(c, n), 200)
+    L.lbm_destroy(c)
+    out["taylor_green_32_fp64"] = {"MLUPS": 32 ** 3 * 200 / t / 1e6, "steps": 200, "bytes_per_lup": 304,
+                                   "note": "launch-bound size; one kernel per step"}
+    return out
+
+
+def _mhd_batch(L, timed, steps, peak, domains):
+    import tempfile
+    out = {}
+
+    # C3: Hartmann channels (64 by default), sizes {32,48,64,96}^3, Ha in [1,20], FP32 MHD,
+    # one persistent cooperative launch per call, captured in a CUDA graph.
+    sweep = inputs.hartmann_batch(domains, seed=2)
+    nu = 0.1
+    shapes = [(n, n, n) for n, _ in sweep]
+    b0s = [2 * ha * nu / n for n, ha in sweep]
+    batch = L.lbm_batch_create(shapes, 1 / (nu / (1 / 3) + 0.5), periodic=(True, False, True), physics="mhd",
+                               precision="fp32", tau_m=0.5 + nu / 0.25,
+                               g=[(8 * nu * 0.01 / n ** 2, 0.0, 0.0) for n, _ in sweep],
+                               b_wall=[(0.0, b, 0.0) for b in b0s])
+    cells = sum(n ** 3 for n, _ in sweep)
+    for k, (n, _) in enumerate(sweep):
+        r, uu, B = inputs.hartmann(n, b0s[k], nx=n, nz=n)
+        L.lbm_init_fields(L.lbm_batch_domain(batch, k), r, uu, B=B)
+    cache = os.path.join(tempfile.gettempdir(), "lbm_tune_cache.json")
+    tuned = L.lbm_autotune(batch, cache)
+    L.lbm_batch_step(batch, 4)
+    n_b = max(20, steps)
+    t = timed(lambda n: L.lbm_batch_step(batch, n), n_b)
+    L.lbm_sync(batch)
+    info = L.lbm_batch_info(batch)
+    L.lbm_destroy(batch)
+    ach = 320 * cells * n_b / t / 1e9
+    out[f"mhd_batch_{domains}"] = {"MLUPS": cells * n_b / t / 1e6, "cells": cells, "steps": n_b, "bytes_per_lup": 320,
+                           "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak, "launch": info,
+                           "autotune_MLUPS": tuned, "launches_per_call": 1}
+    return out
+
+
+def _cgm(L, timed, steps, peak, n):
+    out = {}
+    # C4: colour-gradient droplets n^3 (10% volume, R in [8,24]), FP32.
+    rho, u, phase, spheres, frac = inputs.droplets(n, seed=3)
+    sigma, tau = 1e-4, 0.8
+    alpha_b = 1 / 3
+    alpha_r = 1 - (1 - alpha_b) * 1.0 / 10.0
+    c = L.lbm_create((n, n, n), 1 / tau, physics="cgm", precision="fp32", alpha_r=alpha_r, alpha_b=alpha_b,
+                     A=9 * sigma / tau / 4, beta=0.7)
+    L.lbm_init_fields(c, rho, u, phase=phase)
+    L.lbm_step(c, 3)
+    n_c = max(20, steps // 2)
+    t = timed(lambda k: L.lbm_step(c, k), n_c)
+    L.lbm_reduce(c)
+    L.lbm_destroy(c)
+    ach = 312 * n ** 3 * n_c / t / 1e9
+    out[f"cgm_droplets_{n}"] = {"MLUPS": n ** 3 * n_c / t / 1e6, "steps": n_c, "droplets": len(spheres),
+                               "volume_fraction": frac, "bytes_per_lup": 312, "moved_bytes_per_lup": 464,
+                               "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
+                               "note": "two passes per step (phase field, then collide); 312 B/LUP algorithmic"}
+    return out
+
+
 def time_steps(L, torch, ctx, steps, stream):
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
@@ -240,6 +334,13 @@ def run_ours(args):
 
     n, prec = args.n, args.precision
     stream = torch.cuda.current_stream()
+    if args.only:
+        peak, _ = measured_peaks()
+        res = extra_workloads(L, torch, stream, args.steps, peak, only=args.only, domains=args.domains,
+                              n_cgm=args.n)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "workloads": res}), flush=True)
+        return 0
     rho, u = inputs.noise_box((n, n, n), amp=1e-3, seed=1)
     ctx = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=prec)
     L.lbm_init_fields(ctx, rho, u)
@@ -299,6 +400,11 @@ def run_ours(args):
                "h2d_bytes_per_step": io_bytes / args.steps, "d2h_bytes_per_step": io_bytes / args.steps,
                "note": "lbm_init_fields(pinned host rho,u) + K x lbm_step + lbm_fields(pinned host rho,u)"}
 
+    extra = None
+    if not args.no_variants:
+        extra = extra_workloads(L, torch, stream, args.steps, peak)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_sample()
@@ -313,7 +419,7 @@ def run_ours(args):
                              "kernel": f"fluid_step_kernel<{prec}>",
                              "algorithmic_bytes_per_launch": algorithmic_bytes(n, prec)},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
-                "variants": variants}
+                "variants": variants, "workloads": extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -331,6 +437,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm"], default=None,
+                    help="run one secondary workload alone (profiling)")
+    ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -157,6 +157,43 @@ size_t lbm_state_bytes(const lbm_ctx *ctx);
 lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes);
 
+/* ---- Batched parameter sweeps ---------------------------------------------
+ * Many independent domains (uneven sizes, per-domain omega, force, wall field)
+ * advanced together: each lbm_batch_step runs ONE persistent cooperative
+ * kernel that performs all n steps with a bounded-wait grid barrier between
+ * steps, replayed from a CUDA graph captured on first use (per step count and
+ * buffer parity).  Physics: LBM_PHYS_FLUID or LBM_PHYS_MHD; FP64 or FP32.
+ * grids/relax/forcing/phys are arrays of ndomains entries (forcing may be NULL;
+ * phys is required for MHD).  Domain d is initialised, read back, reduced and
+ * checkpointed through its view (lbm_batch_domain), which accepts
+ * lbm_init_fields, lbm_fields, lbm_reduce and lbm_get/set_populations; the view
+ * is owned by the batch (lbm_destroy on it does nothing, lbm_step on it is
+ * LBM_ERR_UNSUPPORTED).  lbm_step on the batch context equals lbm_batch_step.
+ * A barrier wait longer than 2 s ends the kernel; lbm_sync then returns
+ * LBM_ERR_TIMEOUT. */
+lbm_status lbm_batch_create(lbm_ctx **out, int ndomains, const lbm_grid *grids, const lbm_relax *relax,
+                            const lbm_forcing *forcing, lbm_physics physics, const lbm_physparams *phys,
+                            lbm_precision precision, void *cuda_stream);
+lbm_status lbm_batch_domain(lbm_ctx *batch, int domain, lbm_ctx **view);
+lbm_status lbm_batch_step(lbm_ctx *batch, long n);
+/* Launch shape of the persistent kernel: threads per CTA, CTAs, whether the
+ * launch is replayed from a captured graph, number of tiles per step. */
+lbm_status lbm_batch_info(const lbm_ctx *batch, int *threads, int *grid, int *graph, long *tiles);
+
+/* Diagnostic of the bounded device waits: runs a grid barrier that can never
+ * complete on the current device with the given limit (0 < timeout_s <= 10)
+ * and reports the status word the kernel wrote (LBM_ERR_TIMEOUT expected). */
+lbm_status lbm_barrier_selftest(double timeout_s, int *observed);
+
+/* ---- Autotuner ---------------------------------------------------------------
+ * Chooses the launch shape of a context by timed trials that leave its state
+ * unchanged: threads per block of the single-domain step kernels, or threads
+ * per CTA and CTAs per SM of the batched persistent kernel.  Results are cached
+ * in a JSON file (cache_path, may be NULL = no cache) keyed by device, physics,
+ * precision and geometry; a cached entry is applied without timing unless
+ * force != 0.  Reports the chosen throughput in MLUPS (may be NULL). */
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int force, double *mlups);
+
 /* Allocation-free FP64 reduction of a single-phase population state that the
  * caller owns (the paper has no counterpart; it exists for callers that may
  * not allocate device memory: applications that own all device memory

@@ -282,6 +282,94 @@ def lbm_reduce_state_noalloc(populations, shape, out, *, precision="fp32", perio
         raise LBMError(status, err.value.decode())
 
 
+_lib.lbm_batch_create.argtypes = [ctypes.POINTER(_V), ctypes.c_int, ctypes.POINTER(lbm_grid), ctypes.POINTER(lbm_relax),
+                                  ctypes.POINTER(lbm_forcing), ctypes.c_int, ctypes.POINTER(lbm_physparams),
+                                  ctypes.c_int, _V]
+_lib.lbm_batch_domain.argtypes = [_V, ctypes.c_int, ctypes.POINTER(_V)]
+_lib.lbm_batch_step.argtypes = [_V, ctypes.c_long]
+_lib.lbm_batch_info.argtypes = [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)]
+_lib.lbm_barrier_selftest.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+_lib.lbm_autotune.argtypes = [_V, ctypes.c_char_p, ctypes.c_int, _D]
+for _name in ("lbm_batch_create", "lbm_batch_domain", "lbm_batch_step", "lbm_batch_info", "lbm_barrier_selftest",
+              "lbm_autotune"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+def _scalars(v, nd):
+    """A scalar parameter given once (shared) or once per domain."""
+    return [float(x) for x in v] if isinstance(v, (list, tuple, np.ndarray)) else [float(v)] * nd
+
+
+def _vectors(v, nd):
+    """A 3-vector parameter given once (shared) or once per domain."""
+    if isinstance(v[0], (list, tuple, np.ndarray)):
+        return [tuple(x) for x in v]
+    return [tuple(v)] * nd
+
+
+def lbm_batch_create(shapes, omegas, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
+                     physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), stream=None):
+    """Create a batch of len(shapes) domains; per-domain parameters may be
+    given once (shared) or as lists of one entry per domain."""
+    if _alloc_refs is None and _torch() is not None:
+        lbm_set_allocator(True)
+    nd = len(shapes)
+    omegas = _scalars(omegas, nd)
+    tau_m = _scalars(tau_m, nd)
+    periodic = _vectors(periodic, nd)
+    lid_u = _vectors(lid_u, nd)
+    g = _vectors(g, nd)
+    b_wall = _vectors(b_wall, nd)
+    grids = (lbm_grid * nd)()
+    relax = (lbm_relax * nd)()
+    forc = (lbm_forcing * nd)()
+    phys = (lbm_physparams * nd)()
+    for d in range(nd):
+        grids[d].nx, grids[d].ny, grids[d].nz = (int(v) for v in shapes[d])
+        grids[d].periodic_mask = sum((1 << a) for a in range(3) if periodic[d][a])
+        relax[d] = lbm_relax(float(omegas[d]), 1.0, 1.0, 1.0)
+        phys[d].tau_m = float(tau_m[d])
+        for a in range(3):
+            grids[d].lid_u[a] = float(lid_u[d][a])
+            forc[d].g[a] = float(g[d][a])
+            phys[d].b_wall[a] = float(b_wall[d][a])
+    ctx = _V()
+    s = _current_stream() if stream is None else int(stream)
+    _check(_lib.lbm_batch_create(ctypes.byref(ctx), nd, grids, relax, forc, PHYSICS[physics], phys,
+                                 PRECISIONS[precision], _V(s)))
+    return ctx.value
+
+
+def lbm_batch_domain(ctx, d):
+    v = _V()
+    _check(_lib.lbm_batch_domain(ctx, int(d), ctypes.byref(v)), ctx)
+    return v.value
+
+
+def lbm_batch_step(ctx, n=1):
+    _check(_lib.lbm_batch_step(ctx, int(n)), ctx)
+
+
+def lbm_batch_info(ctx):
+    t, g, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    tiles = ctypes.c_long()
+    _check(_lib.lbm_batch_info(ctx, ctypes.byref(t), ctypes.byref(g), ctypes.byref(gr), ctypes.byref(tiles)), ctx)
+    return {"threads": t.value, "grid": g.value, "graph": bool(gr.value), "tiles": tiles.value}
+
+
+def lbm_barrier_selftest(timeout_s=0.2):
+    obs = ctypes.c_int()
+    _check(_lib.lbm_barrier_selftest(float(timeout_s), ctypes.byref(obs)))
+    return obs.value
+
+
+def lbm_autotune(ctx, cache_path=None, force=False):
+    m = ctypes.c_double()
+    _check(_lib.lbm_autotune(ctx, cache_path.encode() if cache_path else None, int(bool(force)), ctypes.byref(m)), ctx)
+    return m.value
+
+
 def lbm_destroy(ctx):
     if ctx:
         _lib.lbm_destroy(ctx)

@@ -1,0 +1,524 @@
+// lbm_batch.cu -- batched parameter sweeps: many independent domains of
+// uneven sizes advanced by ONE persistent cooperative kernel per call to
+// lbm_batch_step (n steps inside the kernel, a grid-wide barrier between
+// steps), replayed from a captured CUDA graph.
+//
+// Work decomposition: every domain is cut into tiles of `threads` consecutive
+// nodes (x fastest); tiles of all domains form one global index space that the
+// resident CTAs walk with a grid stride.  A CTA finds its tile's domain by a
+// binary search over the per-domain first-tile table (uniform across the CTA).
+// Per-domain parameters (size, boundaries, omega, g, Hartmann field...) come
+// from a small device table.
+//
+// The barrier waits are bounded: a CTA that waits longer than the timeout
+// records LBM_ERR_TIMEOUT and every CTA returns; the host reads the status at
+// the next lbm_sync.  The kernel reads its sources through L2 (ld.global.cg):
+// the buffers are rewritten between barriers, so the read-only L1 path is not
+// valid here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_fluid.cuh"
+#include "lbm_internal.h"
+#include "lbm_mhd.cuh"
+
+namespace lbm {
+
+struct BatchDomain {
+    FluidArgs fl;     // box, omega, g, lid
+    MhdArgs mh;       // box, omega, tau_m, g, b_wall
+    size_t off;       // element offset of the domain's plane 0 in a state copy
+    uint32_t tile0;   // first global tile of the domain
+    uint32_t ntiles;
+};
+
+struct BarrierState {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
+
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-counting grid barrier with a bounded wait.  `expected` is the number
+// of CTAs that must arrive.  Returns false (and every CTA should return) if the
+// wait timed out here or an error was raised elsewhere.
+__device__ bool grid_barrier(BarrierState* bs, unsigned expected, unsigned long long timeout_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &bs->gen;
+        volatile int* verr = &bs->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bs->count, 1u) + 1u;
+        int res = 1;
+        if (arrived == expected) {
+            atomicExch(&bs->count, 0u);
+            __threadfence();
+            atomicAdd(&bs->gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            while (*vgen == g) {
+                if (*verr != 0) {
+                    res = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicCAS(&bs->err, 0, (int)LBM_ERR_TIMEOUT);
+                    res = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = res;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int PHYS, typename S, typename C>
+__global__ void __launch_bounds__(256) batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
+                                                    uint32_t ntiles, long nsteps, int parity0, int dry,
+                                                    BarrierState* bs, unsigned long long timeout_ns) {
+    for (long s = 0; s < nsteps; ++s) {
+        const int par = dry ? parity0 : (int)((parity0 + s) & 1);
+        const S* src = par ? bufB : bufA;
+        S* dst = par ? bufA : bufB;
+        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int lo = 0, hi = nd - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (doms[mid].tile0 <= t)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const BatchDomain& D = doms[lo];
+            const Box& b = D.fl.box;
+            const uint32_t cell = (t - D.tile0) * blockDim.x + threadIdx.x;
+            if (cell < (uint32_t)b.n) {
+                const uint32_t plane = (uint32_t)b.nx * (uint32_t)b.ny;
+                const uint32_t z = cell / plane;
+                const uint32_t r = cell - z * plane;
+                const uint32_t y = r / (uint32_t)b.nx;
+                const uint32_t x = r - y * (uint32_t)b.nx;
+                if (PHYS == LBM_PHYS_MHD)
+                    mhd_node<S, C, true, false>(src + D.off, dst + D.off, D.mh, (int)x, (int)y, (int)z);
+                else
+                    fluid_node<S, C, true, false>(src + D.off, dst + D.off, D.fl, (int)x, (int)y, (int)z);
+            }
+        }
+        if (s + 1 < nsteps && !grid_barrier(bs, gridDim.x, timeout_ns)) return;
+    }
+}
+
+// Diagnostic: a barrier that waits for one CTA more than the grid has, so
+// every wait runs into its (short) limit; used to check that bounded waits
+// end and report LBM_ERR_TIMEOUT.
+__global__ void barrier_selftest_kernel(BarrierState* bs, unsigned long long timeout_ns) {
+    grid_barrier(bs, gridDim.x + 1, timeout_ns);
+}
+
+}  // namespace lbm
+
+using lbm::BarrierState;
+using lbm::BatchDomain;
+
+struct BatchState {
+    int nd = 0;
+    std::vector<lbm_ctx*> views;
+    std::vector<BatchDomain> doms;
+    BatchDomain* d_doms = nullptr;
+    BarrierState* d_bar = nullptr;
+    uint32_t ntiles = 0;
+    int threads = 256;
+    int ctas_per_sm = 0;  // 0 = as many as fit
+    int grid = 0;
+    int sms = 0;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long graph_n[2] = {-1, -1};
+    bool graph_ok = true;
+    size_t state_elems = 0;
+    unsigned long long timeout_ns = lbm::BARRIER_TIMEOUT_NS;
+};
+
+namespace {
+
+template <int PHYS, typename S, typename C>
+void* kernel_ptr() {
+    return (void*)lbm::batch_kernel<PHYS, S, C>;
+}
+
+void* batch_kernel_for(const lbm_ctx* c) {
+    const bool mhd = c->physics == LBM_PHYS_MHD;
+    if (c->prec == LBM_FP64) return mhd ? kernel_ptr<LBM_PHYS_MHD, double, double>() : kernel_ptr<0, double, double>();
+    return mhd ? kernel_ptr<LBM_PHYS_MHD, float, float>() : kernel_ptr<0, float, float>();
+}
+
+void build_tiles(BatchState* B) {
+    uint32_t t = 0;
+    for (auto& d : B->doms) {
+        d.tile0 = t;
+        d.ntiles = (uint32_t)((d.fl.box.n + B->threads - 1) / B->threads);
+        t += d.ntiles;
+    }
+    B->ntiles = t;
+}
+
+cudaError_t configure(lbm_ctx* c) {
+    BatchState* B = c->batch;
+    build_tiles(B);
+    cudaError_t e = cudaMemcpyAsync(B->d_doms, B->doms.data(), sizeof(BatchDomain) * B->nd, cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_for(c), B->threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int want = B->ctas_per_sm > 0 ? std::min(B->ctas_per_sm, per_sm) : per_sm;
+    long grid = (long)want * B->sms;
+    if (grid > (long)B->ntiles) grid = B->ntiles;
+    B->grid = (int)std::max(1L, grid);
+    for (int k = 0; k < 2; ++k) {
+        if (B->graph[k]) cudaGraphExecDestroy(B->graph[k]);
+        B->graph[k] = nullptr;
+        B->graph_n[k] = -1;
+    }
+    return cudaStreamSynchronize(c->stream);
+}
+
+cudaError_t launch_direct(lbm_ctx* c, cudaStream_t st, long n, int parity, int dry) {
+    BatchState* B = c->batch;
+    cudaError_t e = cudaMemsetAsync(B->d_bar, 0, sizeof(BarrierState), st);
+    if (e != cudaSuccess) return e;
+    void* a = c->buf[0];
+    void* b = c->buf[1];
+    BatchDomain* doms = B->d_doms;
+    int nd = B->nd;
+    uint32_t nt = B->ntiles;
+    BarrierState* bar = B->d_bar;
+    unsigned long long to = B->timeout_ns;
+    void* args[] = {&a, &b, &doms, &nd, &nt, &n, &parity, &dry, &bar, &to};
+    return cudaLaunchCooperativeKernel(batch_kernel_for(c), dim3(B->grid), dim3(B->threads), args, 0, st);
+}
+
+// Capture (once per starting parity and step count) and replay.
+cudaError_t run_batch(lbm_ctx* c, long n, int dry) {
+    BatchState* B = c->batch;
+    const int parity = c->cur;
+    cudaError_t e = cudaEventRecord(B->ev_in, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap, B->ev_in, 0);
+    if (e != cudaSuccess) return e;
+    if (dry || !B->graph_ok) {
+        e = launch_direct(c, B->cap, n, parity, dry);
+    } else {
+        if (!B->graph[parity] || B->graph_n[parity] != n) {
+            if (B->graph[parity]) cudaGraphExecDestroy(B->graph[parity]);
+            B->graph[parity] = nullptr;
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t el = launch_direct(c, B->cap, n, parity, 0);
+                e = cudaStreamEndCapture(B->cap, &g);
+                if (e == cudaSuccess) e = el;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph[parity], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                // capture of cooperative launches unavailable: launch directly from now on
+                cudaGetLastError();
+                B->graph_ok = false;
+                B->graph[parity] = nullptr;
+                e = launch_direct(c, B->cap, n, parity, 0);
+            } else {
+                B->graph_n[parity] = n;
+            }
+        }
+        if (B->graph_ok && B->graph[parity]) e = cudaGraphLaunch(B->graph[parity], B->cap);
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(B->ev_out, B->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, B->ev_out, 0);
+    if (e == cudaSuccess && !dry && (n & 1)) {
+        c->cur ^= 1;
+        for (lbm_ctx* v : B->views) v->cur = c->cur;
+    }
+    return e;
+}
+
+}  // namespace
+
+namespace lbm {
+
+// Timed dry run of the persistent kernel (state unchanged) for the autotuner.
+cudaError_t batch_time_config(lbm_ctx* c, int threads, int ctas_per_sm, long steps, float* ms) {
+    BatchState* B = c->batch;
+    B->threads = threads;
+    B->ctas_per_sm = ctas_per_sm;
+    cudaError_t e = configure(c);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    e = run_batch(c, 2, 1);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) e = run_batch(c, steps, 1);
+    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
+cudaError_t batch_apply_config(lbm_ctx* c, int threads, int ctas_per_sm) {
+    c->batch->threads = threads;
+    c->batch->ctas_per_sm = ctas_per_sm;
+    return configure(c);
+}
+
+void batch_destroy(lbm_ctx* c) {
+    BatchState* B = c->batch;
+    if (!B) return;
+    for (int k = 0; k < 2; ++k)
+        if (B->graph[k]) cudaGraphExecDestroy(B->graph[k]);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    for (lbm_ctx* v : B->views) delete v;
+    delete B;
+    c->batch = nullptr;
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, const lbm_relax* relax,
+                            const lbm_forcing* forcing, lbm_physics physics, const lbm_physparams* phys,
+                            lbm_precision precision, void* cuda_stream) {
+    if (!out || ndomains < 1 || !grids || !relax) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (physics != LBM_PHYS_FLUID && physics != LBM_PHYS_MHD) return LBM_ERR_UNSUPPORTED;
+    if (precision != LBM_FP32 && precision != LBM_FP64) return LBM_ERR_UNSUPPORTED;
+    if (physics == LBM_PHYS_MHD && !phys) return LBM_ERR_ARG;
+    const int planes = physics == LBM_PHYS_MHD ? 40 : 19;
+    const size_t elem = precision == LBM_FP64 ? 8 : 4;
+    size_t total = 0, max_plane = 0, cells = 0;
+    for (int d = 0; d < ndomains; ++d) {
+        const lbm_grid& g = grids[d];
+        if (g.nx < 1 || g.ny < 1 || g.nz < 1) return LBM_ERR_ARG;
+        const double n = (double)g.nx * g.ny * g.nz;
+        if (n >= 2147483648.0) return LBM_ERR_ARG;
+        if (!(relax[d].omega > 0.0 && relax[d].omega < 2.0)) return LBM_ERR_ARG;
+        if (relax[d].omega_bulk != 1.0 || relax[d].omega_3 != 1.0 || relax[d].omega_4 != 1.0)
+            return LBM_ERR_UNSUPPORTED;
+        if (physics == LBM_PHYS_MHD && !(phys[d].tau_m > 0.5)) return LBM_ERR_ARG;
+        if (physics == LBM_PHYS_MHD && (g.periodic_mask & 2u) == 0 &&
+            (g.lid_u[0] != 0.0 || g.lid_u[1] != 0.0 || g.lid_u[2] != 0.0))
+            return LBM_ERR_UNSUPPORTED;
+        const size_t nn = (size_t)g.nx * g.ny * g.nz;
+        total += ((size_t)planes * nn + 63) / 64 * 64;  // each domain block starts 256-byte aligned
+        max_plane = std::max(max_plane, (size_t)g.nx * g.ny);
+        cells += nn;
+    }
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    BatchState* B = new (std::nothrow) BatchState();
+    if (!c || !B) {
+        delete c;
+        delete B;
+        return LBM_ERR_OOM;
+    }
+    c->batch = B;
+    c->owns = true;
+    c->grid = grids[0];
+    c->relax = relax[0];
+    if (forcing) c->forcing = forcing[0];
+    c->physics = physics;
+    if (phys) c->phys = phys[0];
+    c->prec = precision;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
+    c->elem = elem;
+    c->planes = planes;
+    c->box.nx = c->box.ny = c->box.nz = 0;
+    c->box.n = cells;
+    B->nd = ndomains;
+    lbm_status st = lbm_internal_alloc_batch(c, total, cells, max_plane);
+    if (st != LBM_OK) {
+        lbm::batch_destroy(c);
+        lbm_internal_release(c);
+        delete c;
+        return st;
+    }
+    B->state_elems = total;
+    cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, c->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
+    size_t off = 0, uoff = 0;
+    for (int d = 0; d < ndomains && e == cudaSuccess; ++d) {
+        const lbm_grid& g = grids[d];
+        BatchDomain D;
+        std::memset(&D, 0, sizeof(D));
+        D.fl.box.nx = g.nx;
+        D.fl.box.ny = g.ny;
+        D.fl.box.nz = g.nz;
+        D.fl.box.periodic = g.periodic_mask & 7u;
+        D.fl.box.n = (size_t)g.nx * g.ny * g.nz;
+        D.fl.omega = relax[d].omega;
+        for (int a = 0; a < 3; ++a) {
+            D.fl.g[a] = forcing ? forcing[d].g[a] : 0.0;
+            D.fl.lid[a] = (g.periodic_mask & 2u) ? 0.0 : g.lid_u[a];
+        }
+        D.mh.box = D.fl.box;
+        D.mh.omega = relax[d].omega;
+        if (physics == LBM_PHYS_MHD) {
+            D.mh.tau_m = phys[d].tau_m;
+            D.mh.inv_tau_m = 1.0 / phys[d].tau_m;
+            for (int a = 0; a < 3; ++a) {
+                D.mh.g[a] = D.fl.g[a];
+                D.mh.bw[a] = phys[d].b_wall[a];
+            }
+        }
+        D.off = off;
+        B->doms.push_back(D);
+        // a view context per domain (init/fields/reduce/populations)
+        lbm_ctx* v = new (std::nothrow) lbm_ctx();
+        if (!v) {
+            e = cudaErrorMemoryAllocation;
+            break;
+        }
+        *v = *c;
+        v->batch = nullptr;
+        v->owns = false;
+        v->parent = c;
+        v->grid = g;
+        v->relax = relax[d];
+        if (forcing) v->forcing = forcing[d];
+        else std::memset(&v->forcing, 0, sizeof(v->forcing));
+        if (phys) v->phys = phys[d];
+        v->box = D.fl.box;
+        v->buf[0] = (char*)c->buf[0] + off * elem;
+        v->buf[1] = (char*)c->buf[1] + off * elem;
+        v->uprev = (char*)c->uprev + uoff * (precision == LBM_FP64 ? 8 : 4);  // compute-type velocities
+        v->block_x = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32));
+        B->views.push_back(v);
+        off += ((size_t)planes * D.fl.box.n + 63) / 64 * 64;
+        uoff += 3 * D.fl.box.n;
+    }
+    if (e == cudaSuccess) e = configure(c);
+    // rest state for every domain
+    for (int d = 0; d < ndomains && e == cudaSuccess; ++d) {
+        lbm_ctx* v = B->views[d];
+        for (int z0 = 0; z0 < v->box.nz && e == cudaSuccess; ++z0) e = lbm_internal_init_slab(v, z0, 1, true);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        lbm::batch_destroy(c);
+        lbm_internal_release(c);
+        delete c;
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_domain(lbm_ctx* c, int d, lbm_ctx** view) {
+    if (!c || !c->batch || !view || d < 0 || d >= c->batch->nd) return LBM_ERR_ARG;
+    c->batch->views[d]->cur = c->cur;
+    *view = c->batch->views[d];
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_ctx* c, long n) {
+    if (!c || !c->batch || n < 0) return LBM_ERR_ARG;
+    if (n == 0) return LBM_OK;
+    cudaError_t e = run_batch(c, n, 0);
+    if (e != cudaSuccess) {
+        c->err = std::string("lbm_batch_step: ") + cudaGetErrorString(e);
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_ctx* c, int* threads, int* grid, int* graph, long* tiles) {
+    if (!c || !c->batch) return LBM_ERR_ARG;
+    if (threads) *threads = c->batch->threads;
+    if (grid) *grid = c->batch->grid;
+    if (graph) *graph = c->batch->graph_ok ? 1 : 0;
+    if (tiles) *tiles = (long)c->batch->ntiles;
+    return LBM_OK;
+}
+
+lbm_status lbm_barrier_selftest(double timeout_s, int* observed) {
+    if (!observed || !(timeout_s > 0.0) || timeout_s > 10.0) return LBM_ERR_ARG;
+    BarrierState* bs = nullptr;
+    if (cudaMalloc(&bs, sizeof(BarrierState)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    cudaError_t e = cudaMemset(bs, 0, sizeof(BarrierState));
+    if (e == cudaSuccess) {
+        lbm::barrier_selftest_kernel<<<4, 64>>>(bs, (unsigned long long)(timeout_s * 1e9));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    BarrierState h;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, bs, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(bs);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    *observed = h.err;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+lbm_status lbm_internal_batch_status(lbm_ctx* c) {
+    if (!c || !c->batch) return LBM_OK;
+    BarrierState h;
+    cudaError_t e = cudaMemcpy(&h, c->batch->d_bar, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    if (h.err == (int)LBM_ERR_TIMEOUT) {
+        c->err = "batch grid barrier wait exceeded its limit";
+        return LBM_ERR_TIMEOUT;
+    }
+    return LBM_OK;
+}
+
+size_t lbm_internal_batch_state_elems(const lbm_ctx* c) { return c->batch ? c->batch->state_elems : 0; }
+
+lbm_status lbm_internal_alloc_batch_tables(lbm_ctx* c) {
+    BatchState* B = c->batch;
+    B->d_doms = (BatchDomain*)lbm_internal_dev_alloc(c, sizeof(BatchDomain) * (size_t)B->nd);
+    B->d_bar = (BarrierState*)lbm_internal_dev_alloc(c, sizeof(BarrierState));
+    if (!B->d_doms || !B->d_bar) return LBM_ERR_OOM;
+    return LBM_OK;
+}
+
+void lbm_internal_free_batch_tables(lbm_ctx* c) {
+    BatchState* B = c->batch;
+    if (!B) return;
+    lbm_internal_dev_free(c, B->d_doms);
+    lbm_internal_dev_free(c, B->d_bar);
+    B->d_doms = nullptr;
+    B->d_bar = nullptr;
+}

@@ -60,17 +60,17 @@ size_t compute_bytes(const lbm_ctx* c) { return c->prec == LBM_FP64 ? 8 : 4; }
 
 int slab_planes(const lbm_ctx* c) {
     const size_t plane = (size_t)c->box.nx * c->box.ny;
-    size_t k = SLAB_TARGET_CELLS / (plane ? plane : 1);
+    size_t k = c->staging_cells / (plane ? plane : 1);  // the staging slab decides
     if (k < 1) k = 1;
     if (k > (size_t)c->box.nz) k = (size_t)c->box.nz;
     return (int)k;
 }
 
-cudaError_t phys_step(lbm_ctx* c, long n) {
+cudaError_t phys_step(lbm_ctx* c, long n, bool dry = false) {
     switch (c->physics) {
-        case LBM_PHYS_FLUID: return lbm::fluid_step(c, n);
-        case LBM_PHYS_MHD: return lbm::mhd_step(c, n);
-        case LBM_PHYS_CGM: return lbm::cgm_step(c, n);
+        case LBM_PHYS_FLUID: return lbm::fluid_step(c, n, dry);
+        case LBM_PHYS_MHD: return lbm::mhd_step(c, n, dry);
+        case LBM_PHYS_CGM: return lbm::cgm_step(c, n, dry);
     }
     return cudaErrorInvalidValue;
 }
@@ -100,6 +100,7 @@ cudaError_t phys_reduce(lbm_ctx* c, bool record) {
 }
 
 void release_all(lbm_ctx* c) {
+    if (!c->owns) return;
     for (int k = 0; k < 2; ++k) dev_free(c, c->buf[k]);
     dev_free(c, c->phi);
     dev_free(c, c->uprev);
@@ -110,6 +111,43 @@ void release_all(lbm_ctx* c) {
 }
 
 }  // namespace
+
+void* lbm_internal_dev_alloc(lbm_ctx* c, size_t bytes) { return dev_alloc(c, bytes); }
+void lbm_internal_dev_free(lbm_ctx* c, void* p) { dev_free(c, p); }
+void lbm_internal_release(lbm_ctx* c) {
+    if (c->batch) lbm_internal_free_batch_tables(c);
+    release_all(c);
+}
+cudaError_t lbm_internal_init_slab(lbm_ctx* c, int z0, int nzs, bool uniform) {
+    return phys_init(c, c->staging, z0, nzs, uniform);
+}
+cudaError_t lbm_internal_step(lbm_ctx* c, long n, bool dry) { return phys_step(c, n, dry); }
+
+// Buffers of a batch: two state copies of `state_elems` values, the residual
+// velocity of every node, reduction scratch, a staging slab sized for the
+// largest domain plane, and the device tables of the persistent kernel.
+lbm_status lbm_internal_alloc_batch(lbm_ctx* c, size_t state_elems, size_t cells, size_t max_plane) {
+    c->alloc = g_alloc;
+    c->release = g_release;
+    c->user = g_user;
+    const size_t cb = compute_bytes(c);
+    size_t k = SLAB_TARGET_CELLS / (max_plane ? max_plane : 1);
+    if (k < 1) k = 1;
+    c->staging_cells = max_plane * k;
+    c->buf[0] = dev_alloc(c, state_elems * c->elem);
+    c->buf[1] = dev_alloc(c, state_elems * c->elem);
+    c->uprev = dev_alloc(c, 3 * cells * cb);
+    c->partials = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH * lbm::RED_BLOCKS);
+    c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
+    c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
+    if (!(c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging)) return LBM_ERR_OOM;
+    if (cudaMallocHost((void**)&c->result_host, sizeof(double) * lbm::RED_WIDTH) != cudaSuccess) {
+        cudaGetLastError();
+        c->result_host = nullptr;
+        return LBM_ERR_OOM;
+    }
+    return lbm_internal_alloc_batch_tables(c);
+}
 
 extern "C" {
 
@@ -236,14 +274,19 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
 }
 
 void lbm_destroy(lbm_ctx* c) {
-    if (!c) return;
+    if (!c || !c->owns) return;  // views of a batch are owned by the batch
     cudaStreamSynchronize(c->stream);
+    if (c->batch) {
+        lbm_internal_free_batch_tables(c);
+        lbm::batch_destroy(c);
+    }
     release_all(c);
     delete c;
 }
 
 lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const double* phase, const double* B) {
     if (!c || !rho) return LBM_ERR_ARG;
+    if (c->batch) return fail(c, LBM_ERR_ARG, "use the per-domain view of a batch (lbm_batch_domain)%s");
     if (c->physics == LBM_PHYS_CGM && !phase) return fail(c, LBM_ERR_ARG, "CGM needs the phase field%s");
     const size_t n = c->box.n, plane = (size_t)c->box.nx * c->box.ny;
     const int nzs = slab_planes(c);
@@ -277,6 +320,8 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const
 
 lbm_status lbm_step(lbm_ctx* c, long n) {
     if (!c || n < 0) return LBM_ERR_ARG;
+    if (c->batch) return lbm_batch_step(c, n);
+    if (!c->owns) return fail(c, LBM_ERR_UNSUPPORTED, "a batch view steps with its batch (lbm_batch_step)%s");
     if (n == 0) return LBM_OK;
     cudaError_t e = phys_step(c, n);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
@@ -287,11 +332,12 @@ lbm_status lbm_sync(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sync");
-    return LBM_OK;
+    return lbm_internal_batch_status(c);
 }
 
 lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* phase, double* B) {
     if (!c) return LBM_ERR_ARG;
+    if (c->batch) return fail(c, LBM_ERR_ARG, "use the per-domain view of a batch (lbm_batch_domain)%s");
     const size_t n = c->box.n, plane = (size_t)c->box.nx * c->box.ny;
     const int nzs = slab_planes(c);
     for (int z0 = 0; z0 < c->box.nz; z0 += nzs) {
@@ -315,6 +361,7 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* phase, double*
 
 lbm_status lbm_reduce(lbm_ctx* c, double* out_mass, double* out_mom, double* out_residual) {
     if (!c) return LBM_ERR_ARG;
+    if (c->batch) return fail(c, LBM_ERR_ARG, "use the per-domain view of a batch (lbm_batch_domain)%s");
     cudaError_t e = phys_reduce(c, true);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->result_host, c->result, sizeof(double) * lbm::RED_WIDTH, cudaMemcpyDeviceToHost,
@@ -344,6 +391,7 @@ lbm_status lbm_reduce(lbm_ctx* c, double* out_mass, double* out_mom, double* out
 lbm_status lbm_run_to_steady(lbm_ctx* c, long max_steps, long check_every, double tol, long* steps_done,
                              double* residual) {
     if (!c || max_steps < 0 || check_every < 1 || !(tol > 0)) return LBM_ERR_ARG;
+    if (c->batch || !c->owns) return fail(c, LBM_ERR_UNSUPPORTED, "steady driver runs on single-domain contexts%s");
     long done = 0;
     double res = -1.0;
     lbm_status s = LBM_OK;
@@ -369,7 +417,11 @@ lbm_status lbm_run_to_steady(lbm_ctx* c, long max_steps, long check_every, doubl
     return s;
 }
 
-size_t lbm_state_bytes(const lbm_ctx* c) { return c ? (size_t)c->planes * c->box.n * c->elem : 0; }
+size_t lbm_state_bytes(const lbm_ctx* c) {
+    if (!c) return 0;
+    if (c->batch) return lbm_internal_batch_state_elems(c) * c->elem;
+    return (size_t)c->planes * c->box.n * c->elem;
+}
 
 lbm_status lbm_get_populations(lbm_ctx* c, void* dst, size_t bytes) {
     if (!c || !dst || bytes != lbm_state_bytes(c)) return LBM_ERR_ARG;

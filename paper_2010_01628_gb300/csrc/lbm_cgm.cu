@@ -302,7 +302,7 @@ static CgmArgs cgm_args(const lbm_ctx* c) {
 }
 
 template <typename S, typename C>
-static cudaError_t step_t(lbm_ctx* c, long n) {
+static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const CgmArgs p = cgm_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
@@ -318,7 +318,7 @@ static cudaError_t step_t(lbm_ctx* c, long n) {
             cgm_phi_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, phi, p);
             cgm_collide_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, dst, phi, p);
         }
-        c->cur ^= 1;
+        if (!dry) c->cur ^= 1;
     }
     return cudaGetLastError();
 }
@@ -357,8 +357,8 @@ static cudaError_t reduce_t(lbm_ctx* c, bool record) {
     return reduce_finalize(c);
 }
 
-cudaError_t cgm_step(lbm_ctx* c, long n) {
-    return c->prec == LBM_FP64 ? step_t<double, double>(c, n) : step_t<float, float>(c, n);
+cudaError_t cgm_step(lbm_ctx* c, long n, bool dry) {
+    return c->prec == LBM_FP64 ? step_t<double, double>(c, n, dry) : step_t<float, float>(c, n, dry);
 }
 cudaError_t cgm_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform) {
     return c->prec == LBM_FP64 ? init_t<double, double>(c, slab, z0, nzs, uniform)

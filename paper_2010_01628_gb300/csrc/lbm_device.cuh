@@ -45,31 +45,38 @@ struct Box {
 // Storage formats.  FP64/FP32 hold f - w (shift by the rest state of rho0 = 1);
 // the 16-bit formats hold (f - w)/w so every direction uses the same range.
 template <typename S> struct Store;
+// load(): read-only path (ld.global.nc), valid when the source buffer is not
+// written during the kernel.  load_cg(): L2-coherent load (ld.global.cg) for
+// kernels that rewrite their sources between grid-wide barriers.
 template <> struct Store<double> {
     static constexpr bool scaled = false;
     __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
+    __device__ static __forceinline__ double load_cg(const double* p) { return __ldcg(p); }
     __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
 };
 template <> struct Store<float> {
     static constexpr bool scaled = false;
     __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
+    __device__ static __forceinline__ float load_cg(const float* p) { return __ldcg(p); }
     __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
 };
 template <> struct Store<__half> {
     static constexpr bool scaled = true;
     __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ float load_cg(const __half* p) { return __half2float(__ldcg(p)); }
     __device__ static __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool scaled = true;
     __device__ static __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ float load_cg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
     __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // Read the shifted population f - w of direction I from storage.
-template <typename S, typename C, int I>
+template <typename S, typename C, int I, bool NC = true>
 __device__ __forceinline__ C load_shifted(const S* p) {
-    C v = (C)Store<S>::load(p);
+    C v = NC ? (C)Store<S>::load(p) : (C)Store<S>::load_cg(p);
     if (Store<S>::scaled) v *= (C)w_of(I);
     return v;
 }
@@ -120,13 +127,13 @@ __device__ __forceinline__ bool pull_source(const Box& b, const Nbr& q, int x, i
 }
 
 // One pulled population f_I(x) = f*_I(x - c_I) (shifted).
-template <typename S, typename C, bool WALLS, int I>
+template <typename S, typename C, bool WALLS, int I, bool NC>
 __device__ __forceinline__ C gather_one(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
                                         uint32_t self, C lx, C ly, C lz) {
     uint32_t cell;
     const bool wall = pull_source<I>(b, q, x, y, z, cell);
-    if (!WALLS || !wall) return load_shifted<S, C, I>(src + (size_t)I * b.n + cell);
-    C v = load_shifted<S, C, opp_of(I)>(src + (size_t)opp_of(I) * b.n + self);
+    if (!WALLS || !wall) return load_shifted<S, C, I, NC>(src + (size_t)I * b.n + cell);
+    C v = load_shifted<S, C, opp_of(I), NC>(src + (size_t)opp_of(I) * b.n + self);
     if (cy_of(I) < 0 && q.wyp)  // source beyond the +y face: the moving lid
         v += (C)(6.0 * w_of(I)) * ((C)cx_of(I) * lx + (C)cy_of(I) * ly + (C)cz_of(I) * lz);
     return v;
@@ -136,10 +143,10 @@ __device__ __forceinline__ C gather_one(const S* __restrict__ src, const Box& b,
 // selects the variant with bounce-back; a pull from behind a wall reads the
 // node's own post-collision population of the opposite direction, plus
 // 6 w_i c_i . u_lid when the wall crossed is the moving +y lid.
-template <typename S, typename C, bool WALLS>
+template <typename S, typename C, bool WALLS, bool NC = true>
 __device__ __forceinline__ void gather19(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
                                          uint32_t self, C lx, C ly, C lz, C (&f)[Q]) {
-#define LBM_G(I) f[I] = gather_one<S, C, WALLS, I>(src, b, q, x, y, z, self, lx, ly, lz);
+#define LBM_G(I) f[I] = gather_one<S, C, WALLS, I, NC>(src, b, q, x, y, z, self, lx, ly, lz);
     LBM_G(0) LBM_G(1) LBM_G(2) LBM_G(3) LBM_G(4) LBM_G(5) LBM_G(6) LBM_G(7) LBM_G(8) LBM_G(9) LBM_G(10)
     LBM_G(11) LBM_G(12) LBM_G(13) LBM_G(14) LBM_G(15) LBM_G(16) LBM_G(17) LBM_G(18)
 #undef LBM_G

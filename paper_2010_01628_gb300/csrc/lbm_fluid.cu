@@ -7,47 +7,18 @@
 // deviatoric central second moments by (1 - omega), set every other central
 // moment to its forced equilibrium value, rebuild f* with the two-step
 // transform of App. C and store it, coalesced, to the other buffer.
+#include "lbm_fluid.cuh"
 #include "lbm_internal.h"
 #include "lbm_reduce.cuh"
 
 namespace lbm {
 
-struct FluidArgs {
-    Box box;
-    double omega;
-    double g[3];
-    double lid[3];
-};
-
-template <typename C>
-__device__ __forceinline__ Macro<C> fluid_macro(const Moments<C>& m, C gx, C gy, C gz) {
-    Macro<C> a;
-    a.rho = (C)1 + m.drho;
-    a.Fx = a.rho * gx;  // F = rho g
-    a.Fy = a.rho * gy;
-    a.Fz = a.rho * gz;
-    const C inv = (C)1 / a.rho;
-    a.ux = (m.jx + (C)0.5 * a.Fx) * inv;
-    a.uy = (m.jy + (C)0.5 * a.Fy) * inv;
-    a.uz = (m.jz + (C)0.5 * a.Fz) * inv;
-    return a;
-}
-
 template <typename S, typename C, bool WALLS>
 __global__ void __launch_bounds__(256) fluid_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                          FluidArgs p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const Box& b = p.box;
-    if (x >= b.nx) return;
-    const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
-    const Nbr q = make_nbr(b, x, y, z);
-    C f[Q];
-    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)p.lid[0], (C)p.lid[1], (C)p.lid[2], f);
-    const Moments<C> m = moments19(f);
-    const Macro<C> a = fluid_macro(m, (C)p.g[0], (C)p.g[1], (C)p.g[2]);
-    collide_fluid<C>(f, m, a, (C)p.omega);
-    scatter19<S, C>(dst, b.n, self, f);
+    if (x >= p.box.nx) return;
+    fluid_node<S, C, WALLS, true>(src, dst, p, x, blockIdx.y, blockIdx.z);
 }
 
 // Equilibrium initialisation of a z-slab from FP64 fields (rho, ux, uy, uz
@@ -137,7 +108,7 @@ static FluidArgs fluid_args(const lbm_ctx* c) {
 }
 
 template <typename S, typename C>
-static cudaError_t step_t(lbm_ctx* c, long n) {
+static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const FluidArgs p = fluid_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
@@ -149,7 +120,7 @@ static cudaError_t step_t(lbm_ctx* c, long n) {
             fluid_step_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, dst, p);
         else
             fluid_step_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, dst, p);
-        c->cur ^= 1;
+        if (!dry) c->cur ^= 1;
     }
     return cudaGetLastError();
 }
@@ -188,12 +159,12 @@ static cudaError_t reduce_t(lbm_ctx* c, bool record) {
     return reduce_finalize(c);
 }
 
-cudaError_t fluid_step(lbm_ctx* c, long n) {
+cudaError_t fluid_step(lbm_ctx* c, long n, bool dry) {
     switch (c->prec) {
-        case LBM_FP64: return step_t<double, double>(c, n);
-        case LBM_FP32: return step_t<float, float>(c, n);
-        case LBM_FP16_SHIFTED: return step_t<__half, float>(c, n);
-        case LBM_BF16_SHIFTED: return step_t<__nv_bfloat16, float>(c, n);
+        case LBM_FP64: return step_t<double, double>(c, n, dry);
+        case LBM_FP32: return step_t<float, float>(c, n, dry);
+        case LBM_FP16_SHIFTED: return step_t<__half, float>(c, n, dry);
+        case LBM_BF16_SHIFTED: return step_t<__nv_bfloat16, float>(c, n, dry);
     }
     return cudaErrorInvalidValue;
 }

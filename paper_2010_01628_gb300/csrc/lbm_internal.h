@@ -8,6 +8,8 @@
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
+struct BatchState;
+
 struct lbm_ctx {
     lbm_grid grid;
     lbm_relax relax;
@@ -36,7 +38,22 @@ struct lbm_ctx {
     void* user;
     int block_x;      // threads per block along x for the step kernels
     std::string err;
+    bool owns = true;            // false for the per-domain views of a batch
+    lbm_ctx* parent = nullptr;   // the batch a view belongs to
+    BatchState* batch = nullptr; // set on a batch context
 };
+
+// Helpers shared between the C-ABI translation units.
+void* lbm_internal_dev_alloc(lbm_ctx* c, size_t bytes);
+void lbm_internal_dev_free(lbm_ctx* c, void* p);
+lbm_status lbm_internal_alloc_batch(lbm_ctx* c, size_t state_elems, size_t cells, size_t max_plane);
+void lbm_internal_release(lbm_ctx* c);
+cudaError_t lbm_internal_init_slab(lbm_ctx* c, int z0, int nzs, bool uniform);
+cudaError_t lbm_internal_step(lbm_ctx* c, long n, bool dry);
+lbm_status lbm_internal_batch_status(lbm_ctx* c);
+lbm_status lbm_internal_alloc_batch_tables(lbm_ctx* c);
+size_t lbm_internal_batch_state_elems(const lbm_ctx* c);
+void lbm_internal_free_batch_tables(lbm_ctx* c);
 
 namespace lbm {
 
@@ -46,23 +63,30 @@ constexpr int RED_BLOCKS = 1216;  // 152 SMs x 8
 constexpr int RED_THREADS = 256;
 
 // Kernel launchers, one per physics module; each returns cudaGetLastError().
-cudaError_t fluid_step(lbm_ctx* c, long n);
+// A "dry" step reads the current state and writes the other buffer without
+// making it current (timing runs of the autotuner leave the state unchanged).
+cudaError_t fluid_step(lbm_ctx* c, long n, bool dry = false);
 cudaError_t fluid_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t fluid_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t fluid_reduce(lbm_ctx* c, bool record);
 
-cudaError_t mhd_step(lbm_ctx* c, long n);
+cudaError_t mhd_step(lbm_ctx* c, long n, bool dry = false);
 cudaError_t mhd_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t mhd_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t mhd_reduce(lbm_ctx* c, bool record);
 
-cudaError_t cgm_step(lbm_ctx* c, long n);
+cudaError_t cgm_step(lbm_ctx* c, long n, bool dry = false);
 cudaError_t cgm_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t cgm_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t cgm_reduce(lbm_ctx* c, bool record);
 
 // Sum RED_BLOCKS partials into c->result (deterministic order).
 cudaError_t reduce_finalize(lbm_ctx* c);
+
+// Batched persistent kernel (lbm_batch.cu).
+cudaError_t batch_time_config(lbm_ctx* c, int threads, int ctas_per_sm, long steps, float* ms);
+cudaError_t batch_apply_config(lbm_ctx* c, int threads, int ctas_per_sm);
+void batch_destroy(lbm_ctx* c);
 
 inline dim3 step_grid(const Box& b, int bx) { return dim3((unsigned)((b.nx + bx - 1) / bx), (unsigned)b.ny, (unsigned)b.nz); }
 

@@ -108,14 +108,19 @@ def droplets(n, seed=3, r_min=8.0, r_max=24.0, fraction=0.10, width=4.0, gap=4.0
         if ok:
             spheres.append((c, r))
             vol += 4.0 / 3.0 * math.pi * r ** 3
-    x, y, z = grid(n, n, n)
     phase = np.full((n, n, n), -1.0)
     for (c, r) in spheres:
-        dx = np.abs(x - c[0]); dx = np.minimum(dx, n - dx)
-        dy = np.abs(y - c[1]); dy = np.minimum(dy, n - dy)
-        dz = np.abs(z - c[2]); dz = np.minimum(dz, n - dz)
-        dist = np.sqrt(dx * dx + dy * dy + dz * dz)
-        phase = np.maximum(phase, np.tanh(2.0 * (r - dist) / width))
+        # the tanh profile is -1 to double precision beyond r + 10 w; work on
+        # the periodic bounding box of that radius
+        reach = int(math.ceil(r + 10.0 * width))
+        idx = [np.arange(int(math.floor(c[a])) - reach, int(math.floor(c[a])) + reach + 2) for a in range(3)]
+        d = [np.abs(idx[a] - c[a]) for a in range(3)]
+        d = [np.minimum(d[a] % n, n - d[a] % n) for a in range(3)]
+        dist = np.sqrt(d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2)
+        prof = np.tanh(2.0 * (r - dist) / width)
+        zi, yi, xi = (idx[2] % n), (idx[1] % n), (idx[0] % n)
+        sub = phase[np.ix_(zi, yi, xi)]
+        phase[np.ix_(zi, yi, xi)] = np.maximum(sub, prof)
     rho = rho_r0 * (1.0 + phase) / 2.0 + rho_b0 * (1.0 - phase) / 2.0
     u = np.zeros((3, n, n, n))
     return rho, u, phase, spheres, vol / total

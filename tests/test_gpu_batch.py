@@ -1,0 +1,154 @@
+"""Batched persistent launch and autotuner on the GPU.
+
+Each domain of a batch must evolve exactly as the same domain run alone (the
+per-node update is shared), and FP64 domains must match the oracle; the
+autotuner must leave the state untouched; the bounded barrier wait must end
+with LBM_ERR_TIMEOUT instead of hanging.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from helpers import oracle_run, rel_l2
+from paper_2010_01628_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def hartmann_domain(n, ha, nu=0.1, u0=0.01):
+    b0 = 2 * ha * nu / n
+    return dict(g=(8 * nu * u0 / n ** 2, 0.0, 0.0), b_wall=(0.0, b0, 0.0), tau_m=0.5 + nu / 0.25,
+                omega=1.0 / (nu / (1 / 3) + 0.5), b0=b0)
+
+
+def mhd_batch_case(sizes_has, precision, steps_list, seed=3):
+    from paper_2010_01628_gb300 import binding as L
+    shapes = [(n, n + 2, n - 1) for n, _ in sizes_has]  # uneven, non-cubic boxes
+    doms = [hartmann_domain(s[1], ha) for s, (_, ha) in zip(shapes, sizes_has)]
+    kw = dict(periodic=(True, False, True), physics="mhd", precision=precision)
+    batch = L.lbm_batch_create(shapes, [d["omega"] for d in doms], g=[d["g"] for d in doms],
+                               b_wall=[d["b_wall"] for d in doms], tau_m=[d["tau_m"] for d in doms], **kw)
+    fields_in = []
+    try:
+        for k, (shape, d) in enumerate(zip(shapes, doms)):
+            rho, u = inputs.random_fields(shape, seed=seed + k, u_amp=0.01)
+            B = np.zeros((3,) + rho.shape)
+            B[1] = d["b0"]
+            fields_in.append((rho, u, B))
+            L.lbm_init_fields(L.lbm_batch_domain(batch, k), rho, u, B=B)
+        for n in steps_list:
+            L.lbm_batch_step(batch, n)
+        L.lbm_sync(batch)
+        info = L.lbm_batch_info(batch)
+        outs = [L.lbm_fields(L.lbm_batch_domain(batch, k), shapes[k], want=("rho", "u", "B")) for k in range(len(shapes))]
+    finally:
+        L.lbm_destroy(batch)
+    return shapes, doms, fields_in, outs, info
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mhd_batch_equals_single_domains(precision):
+    from paper_2010_01628_gb300 import binding as L
+    steps = [3, 4, 3, 5]  # odd counts flip the buffer parity; repeats replay the captured graphs
+    shapes, doms, fin, outs, info = mhd_batch_case([(8, 1.0), (12, 5.0), (6, 20.0), (16, 3.0), (9, 8.0)],
+                                                   precision, steps)
+    assert info["tiles"] > 0 and info["grid"] > 0
+    for k, (shape, d) in enumerate(zip(shapes, doms)):
+        rho, u, B = fin[k]
+        ctx = L.lbm_create(shape, d["omega"], periodic=(True, False, True), physics="mhd", precision=precision,
+                           g=d["g"], b_wall=d["b_wall"], tau_m=d["tau_m"])
+        try:
+            L.lbm_init_fields(ctx, rho, u, B=B)
+            L.lbm_step(ctx, sum(steps))
+            ref = L.lbm_fields(ctx, shape, want=("rho", "u", "B"))
+        finally:
+            L.lbm_destroy(ctx)
+        for f in ("rho", "u", "B"):
+            assert rel_l2(outs[k][f], ref[f]) <= TOL[precision] * 1e-2, (k, f)
+
+
+def test_mhd_batch_fp64_matches_oracle():
+    shapes, doms, fin, outs, info = mhd_batch_case([(8, 2.0), (10, 12.0), (7, 6.0)], "fp64", [7, 6])
+    for k, (shape, d) in enumerate(zip(shapes, doms)):
+        rho, u, B = fin[k]
+        o = oracle_run(shape, d["omega"], 13, rho, u, B=B, physics="mhd", periodic=(True, False, True), g=d["g"],
+                       b_wall=d["b_wall"], tau_m=d["tau_m"])
+        for f in ("rho", "u", "B"):
+            assert rel_l2(outs[k][f], o[f]) <= 1e-12, (k, f)
+
+
+def test_fluid_batch_cavities_match_oracle():
+    """Lid-driven cavities of different sizes and Reynolds numbers in one batch."""
+    from paper_2010_01628_gb300 import binding as L
+    shapes = [(10, 10, 10), (7, 12, 9), (16, 8, 5)]
+    omegas = [1.2, 1.6, 1.9]
+    lids = [(0.05, 0, 0), (0.02, 0, 0.01), (0.08, 0, 0)]
+    b = L.lbm_batch_create(shapes, omegas, periodic=(False, False, False), lid_u=lids, precision="fp64")
+    try:
+        init = []
+        for k, s in enumerate(shapes):
+            rho, u = inputs.random_fields(s, seed=20 + k, u_amp=0.01)
+            init.append((rho, u))
+            L.lbm_init_fields(L.lbm_batch_domain(b, k), rho, u)
+        L.lbm_batch_step(b, 9)
+        outs = [L.lbm_fields(L.lbm_batch_domain(b, k), s) for k, s in enumerate(shapes)]
+    finally:
+        L.lbm_destroy(b)
+    for k, s in enumerate(shapes):
+        o = oracle_run(s, omegas[k], 9, *init[k], periodic=(False, False, False), lid_u=lids[k])
+        assert rel_l2(outs[k]["rho"], o["rho"]) <= 1e-12
+        assert rel_l2(outs[k]["u"], o["u"]) <= 1e-12
+
+
+def test_barrier_wait_is_bounded():
+    """A barrier that can never complete ends after its limit with
+    LBM_ERR_TIMEOUT written by the kernel; the device stays usable."""
+    from paper_2010_01628_gb300 import binding as L
+    assert L.lbm_barrier_selftest(0.2) == L.LBM_ERR_TIMEOUT
+    shapes, doms, fin, outs, info = mhd_batch_case([(8, 2.0), (6, 4.0)], "fp32", [4])
+    assert all(np.isfinite(o["u"]).all() for o in outs)
+
+
+def test_autotune_keeps_state_and_caches(tmp_path):
+    from paper_2010_01628_gb300 import binding as L
+    shape = (64, 32, 16)
+    rho, u = inputs.random_fields(shape, seed=5, u_amp=0.02)
+    cache = str(tmp_path / "tune.json")
+    ctx = L.lbm_create(shape, 1.4, g=(1e-5, 0, 0), precision="fp32")
+    try:
+        L.lbm_init_fields(ctx, rho, u)
+        L.lbm_step(ctx, 3)
+        before = L.lbm_get_populations(ctx).copy()
+        m1 = L.lbm_autotune(ctx, cache)
+        assert m1 > 0
+        np.testing.assert_array_equal(L.lbm_get_populations(ctx), before)
+        m2 = L.lbm_autotune(ctx, cache)  # served from the cache
+        assert m2 == pytest.approx(m1, rel=1e-5)
+        assert os.path.exists(cache) and "fluid|fp32|64x32x16" in open(cache).read()
+        L.lbm_step(ctx, 2)
+    finally:
+        L.lbm_destroy(ctx)
+
+
+def test_batch_autotune_keeps_state(tmp_path):
+    from paper_2010_01628_gb300 import binding as L
+    shapes = [(16, 16, 16), (24, 24, 24), (12, 12, 12)]
+    b = L.lbm_batch_create(shapes, 1.5, periodic=(True, False, True), physics="mhd", precision="fp32",
+                           tau_m=0.9, b_wall=(0, 0.01, 0), g=(1e-6, 0, 0))
+    try:
+        for k, s in enumerate(shapes):
+            rho, u = inputs.random_fields(s, seed=40 + k, u_amp=0.01)
+            L.lbm_init_fields(L.lbm_batch_domain(b, k), rho, u)
+        L.lbm_batch_step(b, 2)
+        before = L.lbm_get_populations(b).copy()
+        m = L.lbm_autotune(b, str(tmp_path / "tune.json"))
+        assert m > 0
+        np.testing.assert_array_equal(L.lbm_get_populations(b), before)
+        L.lbm_batch_step(b, 3)
+        L.lbm_sync(b)
+    finally:
+        L.lbm_destroy(b)
