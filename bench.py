@@ -204,7 +204,7 @@ def run_reference(args):
     return 0
 
 
-def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=256):
+def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=256, tune_cache="tmp"):
     """Throughput of the other configurations of the method, each with its own
     algorithmic bytes per lattice update (populations read + written plus the
     coupled fields).  ``only`` restricts the run to one of them (profiling)."""
@@ -222,7 +222,7 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
     if only in (None, "tg32"):
         out.update(_tg32(L, timed))
     if only in (None, "mhd_batch"):
-        out.update(_mhd_batch(L, timed, steps, peak, domains))
+        out.update(_mhd_batch(L, timed, steps, peak, domains, tune_cache))
     if only in (None, "cgm"):
         out.update(_cgm(L, timed, steps, peak, n_cgm))
     return out
@@ -242,7 +242,7 @@ def _tg32(L, timed):
     return out
 
 
-def _mhd_batch(L, timed, steps, peak, domains):
+def _mhd_batch(L, timed, steps, peak, domains, tune_cache="tmp"):
     import tempfile
     out = {}
 
@@ -260,8 +260,8 @@ def _mhd_batch(L, timed, steps, peak, domains):
     for k, (n, _) in enumerate(sweep):
         r, uu, B = inputs.hartmann(n, b0s[k], nx=n, nz=n)
         L.lbm_init_fields(L.lbm_batch_domain(batch, k), r, uu, B=B)
-    cache = os.path.join(tempfile.gettempdir(), "lbm_tune_cache.json")
-    tuned = L.lbm_autotune(batch, cache)
+    cache = os.path.join(tempfile.gettempdir(), "lbm_tune_cache.json") if tune_cache == "tmp" else None
+    tuned = L.lbm_autotune(batch, cache)  # no cache: every run times the candidates
     L.lbm_batch_step(batch, 4)
     n_b = max(20, steps)
     t = timed(lambda n: L.lbm_batch_step(batch, n), n_b)
@@ -337,7 +337,7 @@ def run_ours(args):
     if args.only:
         peak, _ = measured_peaks()
         res = extra_workloads(L, torch, stream, args.steps, peak, only=args.only, domains=args.domains,
-                              n_cgm=args.n)
+                              n_cgm=args.n, tune_cache=args.tune_cache)
         if rank == 0:
             print(json.dumps({"only": args.only, "workloads": res}), flush=True)
         return 0
@@ -440,6 +440,8 @@ def main():
     ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
+    ap.add_argument("--tune-cache", default="tmp", choices=["tmp", "none"],
+                    help="autotuner cache of the batch workload: a file in the temp dir, or none")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

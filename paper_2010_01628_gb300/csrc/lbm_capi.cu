@@ -234,8 +234,12 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
 
     const size_t state = (size_t)c->planes * c->box.n * c->elem;
     const size_t cb = compute_bytes(c);
-    const int nzs = slab_planes(c);
-    c->staging_cells = (size_t)grid->nx * grid->ny * nzs;
+    const size_t plane = (size_t)grid->nx * grid->ny;
+    size_t kz = SLAB_TARGET_CELLS / plane;
+    if (kz < 1) kz = 1;
+    if (kz > (size_t)grid->nz) kz = (size_t)grid->nz;
+    const int nzs = (int)kz;
+    c->staging_cells = plane * kz;
     c->buf[0] = dev_alloc(c, state);
     c->buf[1] = dev_alloc(c, state);
     c->uprev = dev_alloc(c, 3 * c->box.n * cb);

@@ -21,6 +21,125 @@ __global__ void __launch_bounds__(256) fluid_step_kernel(const S* __restrict__ s
     fluid_node<S, C, WALLS, true>(src, dst, p, x, blockIdx.y, blockIdx.z);
 }
 
+// ---------------------------------------------------------------------------
+// 16-bit storage, two adjacent x-cells per thread.  A thread owns the 32-bit
+// word holding cells (x0, x0+1), x0 even, of every plane: all loads and stores
+// are aligned 4-byte accesses (128 B per warp per plane).  Directions with
+// c_x = +1 need (x0-1, x0): the high half of the previous word, taken from
+// lane-1 by a shuffle (lane 0 and the row start load it); c_x = -1 needs
+// (x0+1, x0+2): the low half of the next word from lane+1 (lane 31 and the row
+// end load it).  Requires nx even.
+template <typename S>
+struct Pair16;
+template <>
+struct Pair16<__half> {
+    __device__ static __forceinline__ float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    __device__ static __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    __device__ static __forceinline__ uint32_t pack(float a, float b) {
+        return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+    }
+};
+template <>
+struct Pair16<__nv_bfloat16> {
+    __device__ static __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
+    __device__ static __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+    __device__ static __forceinline__ uint32_t pack(float a, float b) {
+        return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+    }
+};
+
+struct PairCtx {
+    int x0, lane;
+    bool active;
+    uint32_t self_w;  // word index of the thread's cells within a plane
+    uint32_t plane_w; // words per plane
+};
+
+// Direction I of the thread's two cells, pulled from x - c_I (shifted f - w),
+// with half-way bounce-back replacements.  Every lane of the warp executes the
+// shuffles (inactive lanes past the row end carry zeros).
+template <typename S, bool WALLS, int I>
+__device__ __forceinline__ void gather_pair(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
+                                            const PairCtx& t, int y, int z, float lx, float ly, float lz, float& fa,
+                                            float& fb) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    constexpr float w = (float)w_of(I);
+    const int sy = cy == 0 ? y : (cy > 0 ? q.ym : q.yp);
+    const int sz = cz == 0 ? z : (cz > 0 ? q.zm : q.zp);
+    const bool row_wall = WALLS && ((cy > 0 && q.wym) || (cy < 0 && q.wyp) || (cz > 0 && q.wzm) || (cz < 0 && q.wzp));
+    const uint32_t* P = src + (size_t)I * t.plane_w;
+    const uint32_t row_w = (((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx) >> 1;
+    const uint32_t own = (uint32_t)t.x0 >> 1;
+    const bool ld = t.active && !row_wall;
+    uint32_t wv = ld ? __ldg(P + row_w + own) : 0u;
+    uint32_t val = wv;
+    if (cx > 0) {  // cells need elements (x0 - 1, x0)
+        uint32_t pv = __shfl_up_sync(0xffffffffu, wv, 1);
+        if (t.lane == 0 || t.x0 == 0) pv = ld ? __ldg(P + row_w + (t.x0 == 0 ? (uint32_t)(b.nx - 2) >> 1 : own - 1)) : 0u;
+        val = __byte_perm(pv, wv, 0x5432);
+    } else if (cx < 0) {  // cells need elements (x0 + 1, x0 + 2)
+        uint32_t nv = __shfl_down_sync(0xffffffffu, wv, 1);
+        if (t.lane == 31 || t.x0 + 2 >= b.nx) nv = ld ? __ldg(P + row_w + (t.x0 + 2 >= b.nx ? 0u : own + 1)) : 0u;
+        val = __byte_perm(wv, nv, 0x5432);
+    }
+    fa = Pair16<S>::lo(val) * w;
+    fb = Pair16<S>::hi(val) * w;
+    if (WALLS) {
+        // half-way bounce-back: the node's own post-collision population of the
+        // opposite direction (+ the moving-lid term when the +y face is crossed)
+        const bool wall_a = row_wall || (cx > 0 && q.wxm);
+        const bool wall_b = row_wall || (cx < 0 && t.x0 + 1 == b.nx - 1 && !(b.periodic & 1u));
+        if (wall_a || wall_b) {
+            const uint32_t ov = t.active ? __ldg(src + (size_t)opp_of(I) * t.plane_w + t.self_w) : 0u;
+            const float lid = (cy < 0 && q.wyp) ? (float)(6.0 * w_of(I)) * ((float)cx * lx + (float)cy * ly + (float)cz * lz)
+                                                : 0.f;
+            if (wall_a) fa = Pair16<S>::lo(ov) * w + lid;
+            if (wall_b) fb = Pair16<S>::hi(ov) * w + lid;
+        }
+    }
+}
+
+template <typename S, bool WALLS>
+__global__ void __launch_bounds__(256) fluid_step_pair_kernel(const S* __restrict__ src_, S* __restrict__ dst_,
+                                                              FluidArgs p) {
+    const Box& b = p.box;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(src_);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(dst_);
+    const int y = blockIdx.y, z = blockIdx.z;
+    PairCtx t;
+    t.x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    t.lane = threadIdx.x & 31;
+    t.active = t.x0 < b.nx;
+    t.plane_w = (uint32_t)(b.n >> 1);
+    t.self_w = ((((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx) >> 1) + ((uint32_t)t.x0 >> 1);
+    // x-neighbour flags of cell x0 (left wall) and of the row; the right wall
+    // of cell x0+1 is tested in gather_pair
+    const Nbr q = make_nbr(b, t.active ? t.x0 : 0, y, z);
+    const float lx = (float)p.lid[0], ly = (float)p.lid[1], lz = (float)p.lid[2];
+    float fa[Q], fb[Q];
+#define LBM_GP(I) gather_pair<S, WALLS, I>(src, b, q, t, y, z, lx, ly, lz, fa[I], fb[I]);
+    LBM_GP(0) LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9)
+    LBM_GP(10) LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
+#undef LBM_GP
+    if (!t.active) return;
+    {
+        const Moments<float> m = moments19(fa);
+        const Macro<float> a = fluid_macro(m, (float)p.g[0], (float)p.g[1], (float)p.g[2]);
+        collide_fluid<float>(fa, m, a, (float)p.omega);
+    }
+    {
+        const Moments<float> m = moments19(fb);
+        const Macro<float> a = fluid_macro(m, (float)p.g[0], (float)p.g[1], (float)p.g[2]);
+        collide_fluid<float>(fb, m, a, (float)p.omega);
+    }
+#define LBM_SP(I) \
+    __stcs(dst + (size_t)I * t.plane_w + t.self_w, Pair16<S>::pack(fa[I] * (float)(1.0 / w_of(I)), fb[I] * (float)(1.0 / w_of(I))));
+    LBM_SP(0) LBM_SP(1) LBM_SP(2) LBM_SP(3) LBM_SP(4) LBM_SP(5) LBM_SP(6) LBM_SP(7) LBM_SP(8) LBM_SP(9)
+    LBM_SP(10) LBM_SP(11) LBM_SP(12) LBM_SP(13) LBM_SP(14) LBM_SP(15) LBM_SP(16) LBM_SP(17) LBM_SP(18)
+#undef LBM_SP
+}
+
 // Equilibrium initialisation of a z-slab from FP64 fields (rho, ux, uy, uz
 // planes of nx*ny*nzs values), or of the uniform rest state.
 template <typename S, typename C>
@@ -107,15 +226,32 @@ static FluidArgs fluid_args(const lbm_ctx* c) {
     return p;
 }
 
+template <typename S>
+static constexpr bool is16() {
+    return sizeof(S) == 2;
+}
+
 template <typename S, typename C>
 static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const FluidArgs p = fluid_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
     const dim3 grid = step_grid(c->box, bx);
+    const bool pair = is16<S>() && (c->box.nx % 2 == 0);
+    const dim3 grid2((unsigned)((c->box.nx / 2 + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)c->box.nz);
     for (long s = 0; s < n; ++s) {
         const S* src = (const S*)c->buf[c->cur];
         S* dst = (S*)c->buf[c->cur ^ 1];
+        if constexpr (is16<S>()) {
+            if (pair) {
+                if (walls)
+                    fluid_step_pair_kernel<S, true><<<grid2, bx, 0, c->stream>>>(src, dst, p);
+                else
+                    fluid_step_pair_kernel<S, false><<<grid2, bx, 0, c->stream>>>(src, dst, p);
+                if (!dry) c->cur ^= 1;
+                continue;
+            }
+        }
         if (walls)
             fluid_step_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, dst, p);
         else

@@ -78,6 +78,19 @@ def test_all_wall_combinations_fp64(periodic):
     compare(r, o, 1e-12)
 
 
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape,periodic", [((36, 10, 6), (False, False, True)), ((2, 4, 3), (False, False, False)),
+                                            ((70, 3, 4), (True, True, True))])
+def test_16bit_two_cell_kernel(precision, shape, periodic):
+    """The 16-bit path handles two x-cells per thread (even nx); walls in x,
+    the lid, a two-node row and ragged rows against the FP64 oracle."""
+    rho, u = inputs.random_fields(shape, seed=33, u_amp=0.03)
+    kw = dict(periodic=periodic, lid_u=(0.05, 0.0, 0.01), g=(1e-5, 0.0, 0.0))
+    o = oracle_run(shape, 1.4, 20, rho, u, **kw)
+    r = gpu_run(shape, 1.4, 20, rho, u, precision=precision, **kw)
+    compare(r, o, TOL[precision])
+
+
 def test_uniform_acceleration_momentum_fp32_256():
     """At 256^3 (C2 size, FP32), total momentum grows by exactly M g per step:
     checked with the library's FP64 reductions after 50 steps."""
