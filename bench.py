@@ -298,6 +298,22 @@ def _cgm(L, timed, steps, peak, n):
     return out
 
 
+def apply_launch(L, ctx, spec, tune_cache):
+    """'auto': autotune (timed dry runs, state unchanged); 'direct[:threads]' or
+    'tma:stages:ctas': a fixed launch shape (profiling).  Returns the tuned
+    MLUPS or None."""
+    if spec == "auto":
+        return L.lbm_autotune(ctx, tune_cache)
+    parts = spec.split(":")
+    if parts[0] == "direct":
+        L.lbm_set_launch_shape(ctx, 0, int(parts[1]) if len(parts) > 1 else 256, 0, 1)
+    elif parts[0] == "tma":
+        L.lbm_set_launch_shape(ctx, 1, 256, int(parts[1]), int(parts[2]))
+    else:
+        raise ValueError(spec)
+    return None
+
+
 def time_steps(L, torch, ctx, steps, stream):
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
@@ -342,8 +358,12 @@ def run_ours(args):
             print(json.dumps({"only": args.only, "workloads": res}), flush=True)
         return 0
     rho, u = inputs.noise_box((n, n, n), amp=1e-3, seed=1)
+    import tempfile
+    tune_cache = os.path.join(tempfile.gettempdir(), "lbm_tune_cache.json") if args.tune_cache == "tmp" else None
     ctx = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=prec)
     L.lbm_init_fields(ctx, rho, u)
+    tuned = apply_launch(L, ctx, args.launch, tune_cache)
+    shape = L.lbm_get_launch_shape(ctx)
     L.lbm_step(ctx, args.warmup)
     barrier()
     with ClockSampler(smi_device_id(torch)) as clk:
@@ -356,7 +376,7 @@ def run_ours(args):
     launch_s = t_dev / args.steps
     peak, peak_kind = measured_peaks()
     achieved = algorithmic_bytes(n, prec) / launch_s / 1e9
-    traffic = committed_traffic(f"fluid_step_{prec}_{n}")
+    traffic = committed_traffic(f"fluid_step_{shape['variant']}_{prec}_{n}")
     L.lbm_reduce(ctx)  # divergence check of the timed run (raises on NaN)
     L.lbm_destroy(ctx)
 
@@ -369,6 +389,8 @@ def run_ours(args):
             vsteps = max(10, args.steps // 10)
             c2 = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=vp)
             L.lbm_init_fields(c2, rho, u)
+            apply_launch(L, c2, "auto", tune_cache)
+            vshape = L.lbm_get_launch_shape(c2)
             L.lbm_step(c2, 3)
             barrier()
             tv = max_over_ranks(time_steps(L, torch, c2, vsteps, stream))
@@ -376,7 +398,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
             ach = algorithmic_bytes(n, vp) / (tv / vsteps) / 1e9
             variants[vp] = {"MLUPS": world * cells * vsteps / tv / 1e6, "steps": vsteps,
-                            "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak}
+                            "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak, "launch": vshape}
 
     # End to end through the C ABI with host buffers: upload the initial
     # fields from pinned host memory, K steps, read the fields back.
@@ -387,6 +409,7 @@ def run_ours(args):
         rho_o = torch.empty_like(rho_h).pin_memory()
         u_o = torch.empty_like(u_h).pin_memory()
         c3 = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=prec)
+        apply_launch(L, c3, args.launch, tune_cache)
         barrier()
         t0 = time.perf_counter()
         L.lbm_init_fields(c3, rho_h, u_h)
@@ -413,10 +436,12 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": launch_s * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": DTYPE_NAME[prec], "data": "synthetic",
-                "config": workload_config(n, prec) | {"parallelism": f"replicas x{world}"},
+                "config": workload_config(n, prec) | {"parallelism": f"replicas x{world}", "launch": shape,
+                                                      "autotune_MLUPS": tuned},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": f"fluid_step_kernel<{prec}>",
+                             "kernel": ("fluid_step_tma_kernel" if shape["variant"] == "tma" else
+                                        "fluid_step_kernel") + f"<{prec}>",
                              "algorithmic_bytes_per_launch": algorithmic_bytes(n, prec)},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
                 "variants": variants, "workloads": extra}
@@ -440,6 +465,8 @@ def main():
     ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
+    ap.add_argument("--launch", default="auto",
+                    help="launch shape of the single-phase step: auto | direct[:threads] | tma:stages:ctas")
     ap.add_argument("--tune-cache", default="tmp", choices=["tmp", "none"],
                     help="autotuner cache of the batch workload: a file in the temp dir, or none")
     args = ap.parse_args()

@@ -194,6 +194,16 @@ lbm_status lbm_barrier_selftest(double timeout_s, int *observed);
  * force != 0.  Reports the chosen throughput in MLUPS (may be NULL). */
 lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int force, double *mlups);
 
+/* Set the launch shape of a single-domain context by hand (what lbm_autotune
+ * chooses): variant 0 = one thread per node pulling straight from global
+ * memory (`threads` per block: 32..256, multiple of 32); variant 1 = the
+ * TMA-staged kernel for single-phase flow (x-rows of 19 planes fetched into
+ * shared memory by bulk copies, `stages` rows in flight per CTA, `ctas` CTAs
+ * per SM); it needs nx * bytes-per-value to be a multiple of 16 and enough
+ * shared memory for 2 stages, else LBM_ERR_UNSUPPORTED. */
+lbm_status lbm_set_launch_shape(lbm_ctx *ctx, int variant, int threads, int stages, int ctas);
+lbm_status lbm_get_launch_shape(const lbm_ctx *ctx, int *variant, int *threads, int *stages, int *ctas);
+
 /* Allocation-free FP64 reduction of a single-phase population state that the
  * caller owns (the paper has no counterpart; it exists for callers that may
  * not allocate device memory: applications that own all device memory

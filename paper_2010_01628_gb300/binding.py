@@ -364,6 +364,25 @@ def lbm_barrier_selftest(timeout_s=0.2):
     return obs.value
 
 
+_lib.lbm_set_launch_shape.argtypes = [_V, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+_lib.lbm_set_launch_shape.restype = ctypes.c_int
+
+
+def lbm_set_launch_shape(ctx, variant, threads=256, stages=4, ctas=1):
+    _check(_lib.lbm_set_launch_shape(ctx, int(variant), int(threads), int(stages), int(ctas)), ctx)
+
+
+_lib.lbm_get_launch_shape.argtypes = [_V] + [ctypes.POINTER(ctypes.c_int)] * 4
+_lib.lbm_get_launch_shape.restype = ctypes.c_int
+
+
+def lbm_get_launch_shape(ctx):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(_lib.lbm_get_launch_shape(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return {"variant": ["direct", "tma"][v[0].value], "threads": v[1].value, "stages": v[2].value,
+            "ctas_per_sm": v[3].value}
+
+
 def lbm_autotune(ctx, cache_path=None, force=False):
     m = ctypes.c_double()
     _check(_lib.lbm_autotune(ctx, cache_path.encode() if cache_path else None, int(bool(force)), ctypes.byref(m)), ctx)

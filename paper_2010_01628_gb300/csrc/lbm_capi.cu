@@ -107,7 +107,21 @@ void release_all(lbm_ctx* c) {
     dev_free(c, c->partials);
     dev_free(c, c->result);
     dev_free(c, c->staging);
+    dev_free(c, c->status);
     if (c->result_host) cudaFreeHost(c->result_host);
+}
+
+// Status word of the bounded device waits (TMA-staged kernel); read after a
+// synchronisation.
+lbm_status device_status(lbm_ctx* c) {
+    if (!c->status) return LBM_OK;
+    int h = 0;
+    if (cudaMemcpy(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h == (int)LBM_ERR_TIMEOUT) {
+        c->err = "a bounded device wait (TMA-staged step) exceeded its limit";
+        return LBM_ERR_TIMEOUT;
+    }
+    return LBM_OK;
 }
 
 }  // namespace
@@ -247,7 +261,8 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
     c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
     if (physics == LBM_PHYS_CGM) c->phi = dev_alloc(c, c->box.n * cb);
-    bool ok = c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging &&
+    c->status = (int*)dev_alloc(c, 256);
+    bool ok = c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging && c->status &&
               (physics != LBM_PHYS_CGM || c->phi);
     if (ok && cudaMallocHost((void**)&c->result_host, sizeof(double) * lbm::RED_WIDTH) != cudaSuccess) {
         cudaGetLastError();
@@ -259,12 +274,18 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
         delete c;
         return LBM_ERR_OOM;
     }
+    // Launch shape defaults: the TMA-staged rows for 16-bit single-phase
+    // storage where the geometry allows (the autotuner may change it).
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->tma_stages = lbm::fluid_tma_max_stages(c, 1);
+    c->variant = (c->tma_stages >= 2 && (precision == LBM_FP16_SHIFTED || precision == LBM_BF16_SHIFTED)) ? 1 : 0;
     // Rest state (rho = 1, u = 0; CGM: blue fluid of unit density).
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
     for (int z0 = 0; z0 < grid->nz && e == cudaSuccess; z0 += nzs) {
         const int k = (z0 + nzs <= grid->nz) ? nzs : grid->nz - z0;
         e = phys_init(c, c->staging, z0, k, true);
     }
+
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cuda_fail(c, e, "lbm_create");
@@ -336,6 +357,8 @@ lbm_status lbm_sync(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_sync");
+    const lbm_status st = device_status(c);
+    if (st != LBM_OK) return st;
     return lbm_internal_batch_status(c);
 }
 
@@ -360,7 +383,7 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* phase, double*
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "lbm_fields");
     }
-    return LBM_OK;
+    return device_status(c);
 }
 
 lbm_status lbm_reduce(lbm_ctx* c, double* out_mass, double* out_mom, double* out_residual) {
@@ -372,6 +395,8 @@ lbm_status lbm_reduce(lbm_ctx* c, double* out_mass, double* out_mom, double* out
                             c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_reduce");
+    const lbm_status dst = device_status(c);
+    if (dst != LBM_OK) return dst;
     const double* r = c->result_host;
     const bool had_prev = c->have_prev;
     c->have_prev = true;

@@ -50,24 +50,28 @@ template <typename S> struct Store;
 // kernels that rewrite their sources between grid-wide barriers.
 template <> struct Store<double> {
     static constexpr bool scaled = false;
+    __device__ static __forceinline__ double to_float(double v) { return v; }
     __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
     __device__ static __forceinline__ double load_cg(const double* p) { return __ldcg(p); }
     __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
 };
 template <> struct Store<float> {
     static constexpr bool scaled = false;
+    __device__ static __forceinline__ float to_float(float v) { return v; }
     __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
     __device__ static __forceinline__ float load_cg(const float* p) { return __ldcg(p); }
     __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
 };
 template <> struct Store<__half> {
     static constexpr bool scaled = true;
+    __device__ static __forceinline__ float to_float(__half v) { return __half2float(v); }
     __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
     __device__ static __forceinline__ float load_cg(const __half* p) { return __half2float(__ldcg(p)); }
     __device__ static __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool scaled = true;
+    __device__ static __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
     __device__ static __forceinline__ float load_cg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
     __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
@@ -307,6 +311,52 @@ __device__ __forceinline__ void equilibrium_shifted(C rho, C drho, C ux, C uy, C
     const C t[6] = {z, z, z, z, z, z};
     const C k16c = drho * (C)(1.0 / 9.0);
     back_transform<C>(rho, ux, uy, uz, z, z, z, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX, sm_90+ forms valid on sm_103a).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1D bulk copy global -> shared, completion counted on `bar` (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for phase `parity` of `bar`; false if the deadline passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
 }
 
 }  // namespace lbm

@@ -140,6 +140,133 @@ __global__ void __launch_bounds__(256) fluid_step_pair_kernel(const S* __restric
 #undef LBM_SP
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged persistent step.  Work unit = one x-row (y, z).  For each row the
+// 19 source rows (plane i at (y - c_iy, z - c_iz), whole rows of nx values) are
+// fetched into shared memory by 1D bulk copies that complete on the stage's
+// mbarrier; `stages` rows are in flight per CTA, so the bytes in flight do not
+// cost registers.  x-shifts and the periodic x-wrap are index arithmetic in
+// shared memory; pulls from behind a wall fall back to the node's own opposite
+// population in global memory.  Waits are bounded: on a timeout the CTA writes
+// LBM_ERR_TIMEOUT to `status`, drains its outstanding copies (bounded) and
+// returns.  Requires nx * sizeof(S) to be a multiple of 16 bytes.
+constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;
+
+template <typename S, bool WALLS>
+__device__ __forceinline__ void issue_row(const S* __restrict__ src, const Box& b, S* stage, uint64_t* bar, long r) {
+    const int y = (int)(r % b.ny), z = (int)(r / b.ny);
+    const Nbr q = make_nbr(b, 0, y, z);
+    const uint32_t row_bytes = (uint32_t)b.nx * (uint32_t)sizeof(S);
+    uint32_t bytes = 0;
+#define LBM_RW(I)                                                                                              \
+    const bool w##I = WALLS && ((cy_of(I) > 0 && q.wym) || (cy_of(I) < 0 && q.wyp) || (cz_of(I) > 0 && q.wzm) || \
+                                (cz_of(I) < 0 && q.wzp));                                                      \
+    bytes += w##I ? 0u : row_bytes;
+    LBM_RW(0) LBM_RW(1) LBM_RW(2) LBM_RW(3) LBM_RW(4) LBM_RW(5) LBM_RW(6) LBM_RW(7) LBM_RW(8) LBM_RW(9)
+    LBM_RW(10) LBM_RW(11) LBM_RW(12) LBM_RW(13) LBM_RW(14) LBM_RW(15) LBM_RW(16) LBM_RW(17) LBM_RW(18)
+#undef LBM_RW
+    mbar_arrive_expect_tx(bar, bytes);
+#define LBM_CP(I)                                                                                              \
+    if (!w##I) {                                                                                               \
+        const int sy = cy_of(I) == 0 ? y : (cy_of(I) > 0 ? q.ym : q.yp);                                       \
+        const int sz = cz_of(I) == 0 ? z : (cz_of(I) > 0 ? q.zm : q.zp);                                       \
+        bulk_g2s(stage + (size_t)I * b.nx, src + (size_t)I * b.n + ((size_t)sz * b.ny + sy) * b.nx, row_bytes, bar); \
+    }
+    LBM_CP(0) LBM_CP(1) LBM_CP(2) LBM_CP(3) LBM_CP(4) LBM_CP(5) LBM_CP(6) LBM_CP(7) LBM_CP(8) LBM_CP(9)
+    LBM_CP(10) LBM_CP(11) LBM_CP(12) LBM_CP(13) LBM_CP(14) LBM_CP(15) LBM_CP(16) LBM_CP(17) LBM_CP(18)
+#undef LBM_CP
+}
+
+template <typename S, typename C, bool WALLS, int I>
+__device__ __forceinline__ C pull_staged(const S* __restrict__ stage, const S* __restrict__ src, const Box& b,
+                                         const Nbr& q, int x, int y, int z, uint32_t self, C lx, C ly, C lz) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    if (WALLS) {
+        const bool wall = (cx > 0 && q.wxm) || (cx < 0 && q.wxp) || (cy > 0 && q.wym) || (cy < 0 && q.wyp) ||
+                          (cz > 0 && q.wzm) || (cz < 0 && q.wzp);
+        if (wall) {
+            C v = load_shifted<S, C, opp_of(I)>(src + (size_t)opp_of(I) * b.n + self);
+            if (cy < 0 && q.wyp) v += (C)(6.0 * w_of(I)) * ((C)cx * lx + (C)cy * ly + (C)cz * lz);
+            return v;
+        }
+    }
+    const int sx = cx == 0 ? x : (cx > 0 ? q.xm : q.xp);
+    C v = (C)Store<S>::to_float(stage[(size_t)I * b.nx + sx]);
+    if (Store<S>::scaled) v *= (C)w_of(I);
+    return v;
+}
+
+template <typename S, typename C, bool WALLS>
+__global__ void __launch_bounds__(512, 1) fluid_step_tma_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                                FluidArgs p, int stages, int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int ok;
+    const Box& b = p.box;
+    const size_t stage_elems = (size_t)Q * b.nx;
+    S* sbuf = reinterpret_cast<S*>(smem);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (((size_t)stages * stage_elems * sizeof(S) + 15) & ~size_t(15)));
+    const long rows = (long)b.ny * b.nz;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < stages; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        for (int k = 0; k < stages; ++k) {
+            const long r = blockIdx.x + (long)k * gridDim.x;
+            if (r < rows) issue_row<S, WALLS>(src, b, sbuf + k * stage_elems, &bars[k], r);
+        }
+    }
+    const C lx = (C)p.lid[0], ly = (C)p.lid[1], lz = (C)p.lid[2];
+    const C gx = (C)p.g[0], gy = (C)p.g[1], gz = (C)p.g[2], om = (C)p.omega;
+    long k = 0;
+    for (long r = blockIdx.x; r < rows; r += gridDim.x, ++k) {
+        const int st = (int)(k % stages);
+        const uint32_t parity = (uint32_t)((k / stages) & 1);
+        if (threadIdx.x == 0) ok = mbar_wait_bounded(&bars[st], parity, TMA_WAIT_NS) ? 1 : 0;
+        __syncthreads();
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                atomicExch(status, (int)LBM_ERR_TIMEOUT);
+                // drain the copies this CTA still has in flight (bounded)
+                for (long k2 = k; k2 < k + stages; ++k2) {
+                    const long r2 = blockIdx.x + k2 * gridDim.x;
+                    if (r2 < rows) mbar_wait_bounded(&bars[k2 % stages], (uint32_t)((k2 / stages) & 1), TMA_WAIT_NS);
+                }
+            }
+            return;
+        }
+        // the phase is complete (it cannot advance before this iteration's
+        // final __syncthreads): each thread's own wait returns at once and
+        // orders the bulk-copied data before its reads
+        mbar_wait_bounded(&bars[st], parity, TMA_WAIT_NS);
+        const S* stage = sbuf + st * stage_elems;
+        const int y = (int)(r % b.ny), z = (int)(r / b.ny);
+        for (int x = threadIdx.x; x < b.nx; x += blockDim.x) {
+            const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+            const Nbr q = make_nbr(b, x, y, z);
+            C f[Q];
+#define LBM_PS(I) f[I] = pull_staged<S, C, WALLS, I>(stage, src, b, q, x, y, z, self, lx, ly, lz);
+            LBM_PS(0) LBM_PS(1) LBM_PS(2) LBM_PS(3) LBM_PS(4) LBM_PS(5) LBM_PS(6) LBM_PS(7) LBM_PS(8) LBM_PS(9)
+            LBM_PS(10) LBM_PS(11) LBM_PS(12) LBM_PS(13) LBM_PS(14) LBM_PS(15) LBM_PS(16) LBM_PS(17) LBM_PS(18)
+#undef LBM_PS
+            const Moments<C> m = moments19(f);
+            const Macro<C> a = fluid_macro(m, gx, gy, gz);
+            collide_fluid<C>(f, m, a, om);
+            scatter19<S, C>(dst, b.n, self, f);
+        }
+        __syncthreads();  // stage `st` fully read
+        if (threadIdx.x == 0) {
+            const long r2 = r + (long)stages * gridDim.x;
+            if (r2 < rows) {
+                fence_proxy_async();
+                issue_row<S, WALLS>(src, b, sbuf + st * stage_elems, &bars[st], r2);
+            }
+        }
+    }
+}
+
 // Equilibrium initialisation of a z-slab from FP64 fields (rho, ux, uy, uz
 // planes of nx*ny*nzs values), or of the uniform rest state.
 template <typename S, typename C>
@@ -231,11 +358,54 @@ static constexpr bool is16() {
     return sizeof(S) == 2;
 }
 
+constexpr size_t TMA_SMEM_LIMIT = 227 * 1024;
+
+static size_t tma_stage_bytes(const lbm_ctx* c) { return (size_t)Q * c->box.nx * c->elem; }
+
+int fluid_tma_max_stages(const lbm_ctx* c, int ctas) {
+    if (c->physics != LBM_PHYS_FLUID || ctas < 1) return 0;
+    if (((size_t)c->box.nx * c->elem) % 16 != 0 || c->box.nx < 32) return 0;
+    const size_t per_cta = TMA_SMEM_LIMIT / (size_t)ctas - 1024;
+    long st = (long)(per_cta / tma_stage_bytes(c));
+    if (st > 8) st = 8;
+    return st >= 2 ? (int)st : 0;
+}
+
+template <typename S, typename C, bool WALLS>
+static cudaError_t launch_tma(lbm_ctx* c, const S* src, S* dst, const FluidArgs& p) {
+    const int stages = c->tma_stages;
+    const size_t smem = (((size_t)stages * tma_stage_bytes(c) + 15) & ~size_t(15)) + (size_t)stages * 8;
+    static size_t configured = 0;  // per instantiation: largest dynamic smem granted so far
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(fluid_step_tma_kernel<S, C, WALLS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM_LIMIT);
+        if (e != cudaSuccess) return e;
+        configured = TMA_SMEM_LIMIT;
+    }
+    const long rows = (long)c->box.ny * c->box.nz;
+    long grid = (long)c->sms * c->tma_ctas;
+    if (grid > rows) grid = rows;
+    int block = ((c->box.nx + 31) / 32) * 32;
+    if (block > 512) block = 512;
+    fluid_step_tma_kernel<S, C, WALLS><<<(unsigned)grid, block, smem, c->stream>>>(src, dst, p, stages, c->status);
+    return cudaSuccess;
+}
+
 template <typename S, typename C>
 static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const FluidArgs p = fluid_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
+    if (c->variant == 1 && c->tma_stages >= 2 && c->tma_stages <= fluid_tma_max_stages(c, c->tma_ctas)) {
+        for (long s = 0; s < n; ++s) {
+            const S* src = (const S*)c->buf[c->cur];
+            S* dst = (S*)c->buf[c->cur ^ 1];
+            cudaError_t e = walls ? launch_tma<S, C, true>(c, src, dst, p) : launch_tma<S, C, false>(c, src, dst, p);
+            if (e != cudaSuccess) return e;
+            if (!dry) c->cur ^= 1;
+        }
+        return cudaGetLastError();
+    }
     const dim3 grid = step_grid(c->box, bx);
     const bool pair = is16<S>() && (c->box.nx % 2 == 0);
     const dim3 grid2((unsigned)((c->box.nx / 2 + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)c->box.nz);

@@ -37,6 +37,11 @@ struct lbm_ctx {
     lbm_free_fn release;
     void* user;
     int block_x;      // threads per block along x for the step kernels
+    int variant = 0;  // single-phase step: 0 = direct pulls, 1 = TMA-staged rows
+    int tma_stages = 0;
+    int tma_ctas = 1; // CTAs per SM of the TMA-staged kernel
+    int sms = 0;
+    int* status = nullptr;  // device status word written by bounded waits
     std::string err;
     bool owns = true;            // false for the per-domain views of a batch
     lbm_ctx* parent = nullptr;   // the batch a view belongs to
@@ -66,6 +71,9 @@ constexpr int RED_THREADS = 256;
 // A "dry" step reads the current state and writes the other buffer without
 // making it current (timing runs of the autotuner leave the state unchanged).
 cudaError_t fluid_step(lbm_ctx* c, long n, bool dry = false);
+// Largest stage count of the TMA-staged kernel that fits `ctas` CTAs per SM (0
+// if the geometry does not allow the variant).
+int fluid_tma_max_stages(const lbm_ctx* c, int ctas);
 cudaError_t fluid_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t fluid_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t fluid_reduce(lbm_ctx* c, bool record);

@@ -151,6 +151,33 @@ float time_dry_steps(lbm_ctx* c, long reps, cudaError_t* err) {
 
 }  // namespace
 
+extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads, int stages, int ctas) {
+    if (!c || c->batch || !c->owns) return LBM_ERR_ARG;
+    if (threads < 32 || threads > 256 || threads % 32 != 0) return LBM_ERR_ARG;
+    if (variant == 0) {
+        c->variant = 0;
+        c->block_x = threads;
+        return LBM_OK;
+    }
+    if (variant != 1) return LBM_ERR_ARG;
+    if (ctas < 1 || stages < 2) return LBM_ERR_ARG;
+    if (stages > lbm::fluid_tma_max_stages(c, ctas)) return LBM_ERR_UNSUPPORTED;
+    c->variant = 1;
+    c->block_x = threads;
+    c->tma_stages = stages;
+    c->tma_ctas = ctas;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_launch_shape(const lbm_ctx* c, int* variant, int* threads, int* stages, int* ctas) {
+    if (!c || c->batch) return LBM_ERR_ARG;
+    if (variant) *variant = c->variant;
+    if (threads) *threads = c->block_x;
+    if (stages) *stages = c->variant == 1 ? c->tma_stages : 0;
+    if (ctas) *ctas = c->variant == 1 ? c->tma_ctas : 0;
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force, double* mlups) {
     if (!c) return LBM_ERR_ARG;
     if (!c->owns) return LBM_ERR_UNSUPPORTED;
@@ -172,14 +199,25 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
 
     auto hit = cache.find(key);
     if (!force && hit != cache.end() && hit->second.count("threads")) {
-        const int threads = (int)hit->second["threads"];
+        Entry& h = hit->second;
+        const int threads = (int)h["threads"];
         if (c->batch) {
-            const int cps = hit->second.count("ctas_per_sm") ? (int)hit->second["ctas_per_sm"] : 0;
+            const int cps = h.count("ctas_per_sm") ? (int)h["ctas_per_sm"] : 0;
             if (lbm::batch_apply_config(c, threads, cps) != cudaSuccess) return LBM_ERR_CUDA;
         } else {
             c->block_x = threads;
+            const int variant = h.count("variant") ? (int)h["variant"] : 0;
+            const int stages = h.count("stages") ? (int)h["stages"] : 0;
+            const int ctas = h.count("ctas") ? (int)h["ctas"] : 1;
+            if (variant == 1 && stages >= 2 && stages <= lbm::fluid_tma_max_stages(c, ctas)) {
+                c->variant = 1;
+                c->tma_stages = stages;
+                c->tma_ctas = ctas;
+            } else {
+                c->variant = 0;
+            }
         }
-        if (mlups) *mlups = hit->second.count("mlups") ? hit->second["mlups"] : 0.0;
+        if (mlups) *mlups = h.count("mlups") ? h["mlups"] : 0.0;
         return LBM_OK;
     }
 
@@ -207,10 +245,22 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
         if (lbm::batch_apply_config(c, (int)best["threads"], (int)best["ctas_per_sm"]) != cudaSuccess)
             return LBM_ERR_CUDA;
     } else {
-        const int cand[] = {32, 64, 128, 256};
-        const int saved = c->block_x;
-        for (int bx : cand) {
-            c->block_x = bx;
+        struct Cand {
+            int variant, threads, stages, ctas;
+        };
+        std::vector<Cand> cands;
+        for (int bx : {64, 128, 256}) cands.push_back({0, bx, 0, 1});
+        for (int ctas : {1, 2}) {
+            const int smax = lbm::fluid_tma_max_stages(c, ctas);
+            for (int st : {2, 3, 4, 6, 8})
+                if (st <= smax) cands.push_back({1, c->block_x, st, ctas});
+        }
+        const int saved_bx = c->block_x, saved_var = c->variant, saved_st = c->tma_stages, saved_ct = c->tma_ctas;
+        for (const Cand& k : cands) {
+            c->variant = k.variant;
+            c->block_x = k.threads;
+            c->tma_stages = k.stages > 0 ? k.stages : saved_st;
+            c->tma_ctas = k.ctas;
             float one = time_dry_steps(c, 1, &e);  // warm-up and size estimate
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -227,14 +277,25 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
             const double per = ms / reps;
             if (per < best_ms) {
                 best_ms = per;
-                best = Entry{{"threads", (double)bx}};
+                best = Entry{{"variant", (double)k.variant},
+                             {"threads", (double)k.threads},
+                             {"stages", (double)k.stages},
+                             {"ctas", (double)k.ctas}};
             }
         }
         if (best.empty()) {
-            c->block_x = saved;
+            c->block_x = saved_bx;
+            c->variant = saved_var;
+            c->tma_stages = saved_st;
+            c->tma_ctas = saved_ct;
             return LBM_ERR_CUDA;
         }
         c->block_x = (int)best["threads"];
+        c->variant = (int)best["variant"];
+        if (c->variant == 1) {
+            c->tma_stages = (int)best["stages"];
+            c->tma_ctas = (int)best["ctas"];
+        }
     }
     best["mlups"] = cells / (best_ms * 1e-3) / 1e6;
     if (mlups) *mlups = best["mlups"];

@@ -26,11 +26,14 @@ def oracle_run(shape, omega, steps, rho, u, phase=None, B=None, closed_form=True
     return {"rho": r, "u": uu, "phase": ph, "B": BB, "domain": d}
 
 
-def gpu_run(shape, omega, steps, rho, u, phase=None, B=None, precision="fp64", physics="fluid", keep=False, **kw):
+def gpu_run(shape, omega, steps, rho, u, phase=None, B=None, precision="fp64", physics="fluid", keep=False,
+            launch=None, **kw):
     from paper_2010_01628_gb300 import binding as L
 
     ctx = L.lbm_create(shape, omega, physics=physics, precision=precision, **kw)
     try:
+        if launch is not None:
+            L.lbm_set_launch_shape(ctx, *launch)
         L.lbm_init_fields(ctx, np.ascontiguousarray(rho), np.ascontiguousarray(u),
                           None if phase is None else np.ascontiguousarray(phase),
                           None if B is None else np.ascontiguousarray(B))
