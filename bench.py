@@ -305,8 +305,8 @@ def apply_launch(L, ctx, spec, tune_cache):
     if spec == "auto":
         return L.lbm_autotune(ctx, tune_cache)
     parts = spec.split(":")
-    if parts[0] == "direct":
-        L.lbm_set_launch_shape(ctx, 0, int(parts[1]) if len(parts) > 1 else 256, 0, 1)
+    if parts[0] in ("direct", "pair"):
+        L.lbm_set_launch_shape(ctx, 0 if parts[0] == "direct" else 2, int(parts[1]) if len(parts) > 1 else 256, 0, 1)
     elif parts[0] == "tma":
         L.lbm_set_launch_shape(ctx, 1, 256, int(parts[1]), int(parts[2]))
     else:
@@ -440,8 +440,8 @@ def run_ours(args):
                                                       "autotune_MLUPS": tuned},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": ("fluid_step_tma_kernel" if shape["variant"] == "tma" else
-                                        "fluid_step_kernel") + f"<{prec}>",
+                             "kernel": {"tma": "fluid_step_tma_kernel", "pair": "fluid_step_pair_kernel"}.get(
+                                 shape["variant"], "fluid_step_kernel") + f"<{prec}>",
                              "algorithmic_bytes_per_launch": algorithmic_bytes(n, prec)},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
                 "variants": variants, "workloads": extra}
@@ -466,7 +466,8 @@ def main():
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     ap.add_argument("--launch", default="auto",
-                    help="launch shape of the single-phase step: auto | direct[:threads] | tma:stages:ctas")
+                    help="launch shape of the single-phase step: auto | direct[:threads] | pair[:threads] | "
+                         "tma:stages:ctas")
     ap.add_argument("--tune-cache", default="tmp", choices=["tmp", "none"],
                     help="autotuner cache of the batch workload: a file in the temp dir, or none")
     args = ap.parse_args()

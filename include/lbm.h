@@ -196,7 +196,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int force, double 
 
 /* Set the launch shape of a single-domain context by hand (what lbm_autotune
  * chooses): variant 0 = one thread per node pulling straight from global
- * memory (`threads` per block: 32..256, multiple of 32); variant 1 = the
+ * memory (`threads` per block: 32..256, multiple of 32); variant 2 = two
+ * x-neighbour nodes per thread with aligned 32-bit accesses (16-bit storage,
+ * even nx, single phase); variant 1 = the
  * TMA-staged kernel for single-phase flow (x-rows of 19 planes fetched into
  * shared memory by bulk copies, `stages` rows in flight per CTA, `ctas` CTAs
  * per SM); it needs nx * bytes-per-value to be a multiple of 16 and enough

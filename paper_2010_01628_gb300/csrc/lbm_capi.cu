@@ -274,11 +274,11 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
         delete c;
         return LBM_ERR_OOM;
     }
-    // Launch shape defaults: the TMA-staged rows for 16-bit single-phase
-    // storage where the geometry allows (the autotuner may change it).
+    // Launch shape default: direct pulls, one node per thread (lbm_autotune
+    // or lbm_set_launch_shape may select the staged or paired kernels).
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     c->tma_stages = lbm::fluid_tma_max_stages(c, 1);
-    c->variant = (c->tma_stages >= 2 && (precision == LBM_FP16_SHIFTED || precision == LBM_BF16_SHIFTED)) ? 1 : 0;
+    c->variant = 0;
     // Rest state (rho = 1, u = 0; CGM: blue fluid of unit density).
     cudaError_t e = cudaMemsetAsync(c->status, 0, 256, c->stream);
     for (int z0 = 0; z0 < grid->nz && e == cudaSuccess; z0 += nzs) {

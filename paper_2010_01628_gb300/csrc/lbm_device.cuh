@@ -25,6 +25,13 @@ __host__ __device__ constexpr int cz_of(int i) {
     constexpr int t[19] = {0, 0, 0, -1, 0, 0, -1, 1, -1, 1, 0, 0, 1, 0, 0, 1, -1, 1, -1};
     return t[i];
 }
+// Runtime-index variants (for per-lane direction work).
+__host__ __device__ __forceinline__ int cy_of_rt(int i) {
+    return (i == 2 || i == 4 || i == 8 || i == 9 || i == 14) ? -1 : ((i == 5 || i == 11 || i == 13 || i == 17 || i == 18) ? 1 : 0);
+}
+__host__ __device__ __forceinline__ int cz_of_rt(int i) {
+    return (i == 3 || i == 6 || i == 8 || i == 16 || i == 18) ? -1 : ((i == 7 || i == 9 || i == 12 || i == 15 || i == 17) ? 1 : 0);
+}
 __host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
 __host__ __device__ constexpr double w_of(int i) {
     return i == 0 ? 1.0 / 3.0

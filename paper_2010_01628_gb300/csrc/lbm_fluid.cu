@@ -152,29 +152,27 @@ __global__ void __launch_bounds__(256) fluid_step_pair_kernel(const S* __restric
 // returns.  Requires nx * sizeof(S) to be a multiple of 16 bytes.
 constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;
 
+// Issue the bulk copies of row r's 19 source rows into `stage` (warp 0: lane 0
+// registers the expected bytes, then lanes 0..18 issue one copy each).
 template <typename S, bool WALLS>
-__device__ __forceinline__ void issue_row(const S* __restrict__ src, const Box& b, S* stage, uint64_t* bar, long r) {
+__device__ __forceinline__ void issue_row(const S* __restrict__ src, const Box& b, S* stage, uint64_t* bar, long r,
+                                          int lane) {
     const int y = (int)(r % b.ny), z = (int)(r / b.ny);
     const Nbr q = make_nbr(b, 0, y, z);
     const uint32_t row_bytes = (uint32_t)b.nx * (uint32_t)sizeof(S);
-    uint32_t bytes = 0;
-#define LBM_RW(I)                                                                                              \
-    const bool w##I = WALLS && ((cy_of(I) > 0 && q.wym) || (cy_of(I) < 0 && q.wyp) || (cz_of(I) > 0 && q.wzm) || \
-                                (cz_of(I) < 0 && q.wzp));                                                      \
-    bytes += w##I ? 0u : row_bytes;
-    LBM_RW(0) LBM_RW(1) LBM_RW(2) LBM_RW(3) LBM_RW(4) LBM_RW(5) LBM_RW(6) LBM_RW(7) LBM_RW(8) LBM_RW(9)
-    LBM_RW(10) LBM_RW(11) LBM_RW(12) LBM_RW(13) LBM_RW(14) LBM_RW(15) LBM_RW(16) LBM_RW(17) LBM_RW(18)
-#undef LBM_RW
-    mbar_arrive_expect_tx(bar, bytes);
-#define LBM_CP(I)                                                                                              \
-    if (!w##I) {                                                                                               \
-        const int sy = cy_of(I) == 0 ? y : (cy_of(I) > 0 ? q.ym : q.yp);                                       \
-        const int sz = cz_of(I) == 0 ? z : (cz_of(I) > 0 ? q.zm : q.zp);                                       \
-        bulk_g2s(stage + (size_t)I * b.nx, src + (size_t)I * b.n + ((size_t)sz * b.ny + sy) * b.nx, row_bytes, bar); \
+    // lane i < 19 handles direction i; a source row behind a wall is not fetched
+    int i = lane < Q ? lane : 0;
+    const int cy = cy_of_rt(i), cz = cz_of_rt(i);
+    const bool wall = WALLS && ((cy > 0 && q.wym) || (cy < 0 && q.wyp) || (cz > 0 && q.wzm) || (cz < 0 && q.wzp));
+    const bool mine = lane < Q && !wall;
+    const unsigned fetch = __ballot_sync(0xffffffffu, mine);
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)__popc(fetch) * row_bytes);
+    __syncwarp();
+    if (mine) {
+        const int sy = cy == 0 ? y : (cy > 0 ? q.ym : q.yp);
+        const int sz = cz == 0 ? z : (cz > 0 ? q.zm : q.zp);
+        bulk_g2s(stage + (size_t)i * b.nx, src + (size_t)i * b.n + ((size_t)sz * b.ny + sy) * b.nx, row_bytes, bar);
     }
-    LBM_CP(0) LBM_CP(1) LBM_CP(2) LBM_CP(3) LBM_CP(4) LBM_CP(5) LBM_CP(6) LBM_CP(7) LBM_CP(8) LBM_CP(9)
-    LBM_CP(10) LBM_CP(11) LBM_CP(12) LBM_CP(13) LBM_CP(14) LBM_CP(15) LBM_CP(16) LBM_CP(17) LBM_CP(18)
-#undef LBM_CP
 }
 
 template <typename S, typename C, bool WALLS, int I>
@@ -197,25 +195,25 @@ __device__ __forceinline__ C pull_staged(const S* __restrict__ stage, const S* _
 }
 
 template <typename S, typename C, bool WALLS>
-__global__ void __launch_bounds__(512, 1) fluid_step_tma_kernel(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(256, 4) fluid_step_tma_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                                 FluidArgs p, int stages, int* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int ok;
     const Box& b = p.box;
     const size_t stage_elems = (size_t)Q * b.nx;
     S* sbuf = reinterpret_cast<S*>(smem);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (((size_t)stages * stage_elems * sizeof(S) + 15) & ~size_t(15)));
     const long rows = (long)b.ny * b.nz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int k = 0; k < stages; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
         fence_proxy_async();
         for (int k = 0; k < stages; ++k) {
             const long r = blockIdx.x + (long)k * gridDim.x;
-            if (r < rows) issue_row<S, WALLS>(src, b, sbuf + k * stage_elems, &bars[k], r);
+            if (r < rows) issue_row<S, WALLS>(src, b, sbuf + k * stage_elems, &bars[k], r, lane);
         }
     }
     const C lx = (C)p.lid[0], ly = (C)p.lid[1], lz = (C)p.lid[2];
@@ -224,9 +222,10 @@ __global__ void __launch_bounds__(512, 1) fluid_step_tma_kernel(const S* __restr
     for (long r = blockIdx.x; r < rows; r += gridDim.x, ++k) {
         const int st = (int)(k % stages);
         const uint32_t parity = (uint32_t)((k / stages) & 1);
-        if (threadIdx.x == 0) ok = mbar_wait_bounded(&bars[st], parity, TMA_WAIT_NS) ? 1 : 0;
-        __syncthreads();
-        if (!ok) {
+        // every thread waits (bounded) for the stage; the vote makes the
+        // continue/stop decision uniform across the CTA
+        const bool ready = mbar_wait_bounded(&bars[st], parity, TMA_WAIT_NS);
+        if (!__syncthreads_and(ready)) {
             if (threadIdx.x == 0) {
                 atomicExch(status, (int)LBM_ERR_TIMEOUT);
                 // drain the copies this CTA still has in flight (bounded)
@@ -237,10 +236,6 @@ __global__ void __launch_bounds__(512, 1) fluid_step_tma_kernel(const S* __restr
             }
             return;
         }
-        // the phase is complete (it cannot advance before this iteration's
-        // final __syncthreads): each thread's own wait returns at once and
-        // orders the bulk-copied data before its reads
-        mbar_wait_bounded(&bars[st], parity, TMA_WAIT_NS);
         const S* stage = sbuf + st * stage_elems;
         const int y = (int)(r % b.ny), z = (int)(r / b.ny);
         for (int x = threadIdx.x; x < b.nx; x += blockDim.x) {
@@ -257,11 +252,11 @@ __global__ void __launch_bounds__(512, 1) fluid_step_tma_kernel(const S* __restr
             scatter19<S, C>(dst, b.n, self, f);
         }
         __syncthreads();  // stage `st` fully read
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
             const long r2 = r + (long)stages * gridDim.x;
             if (r2 < rows) {
                 fence_proxy_async();
-                issue_row<S, WALLS>(src, b, sbuf + st * stage_elems, &bars[st], r2);
+                issue_row<S, WALLS>(src, b, sbuf + st * stage_elems, &bars[st], r2, lane);
             }
         }
     }
@@ -358,35 +353,48 @@ static constexpr bool is16() {
     return sizeof(S) == 2;
 }
 
-constexpr size_t TMA_SMEM_LIMIT = 227 * 1024;
+// Shared-memory budget of one CTA of the staged kernel: the opt-in maximum per
+// block (227 KB) with one CTA per SM, else an even share of the SM's 228 KB
+// less the 1 KB the runtime reserves per CTA; 256 bytes are kept for the
+// kernel's static shared memory.
+constexpr size_t SMEM_PER_BLOCK_OPTIN = 227 * 1024;
+constexpr size_t SMEM_PER_SM = 228 * 1024;
 
 static size_t tma_stage_bytes(const lbm_ctx* c) { return (size_t)Q * c->box.nx * c->elem; }
+static size_t tma_smem_bytes(const lbm_ctx* c, int stages) {
+    return (((size_t)stages * tma_stage_bytes(c) + 15) & ~size_t(15)) + (size_t)stages * 8;
+}
 
 int fluid_tma_max_stages(const lbm_ctx* c, int ctas) {
-    if (c->physics != LBM_PHYS_FLUID || ctas < 1) return 0;
+    if (c->physics != LBM_PHYS_FLUID || ctas < 1 || ctas > 4) return 0;
     if (((size_t)c->box.nx * c->elem) % 16 != 0 || c->box.nx < 32) return 0;
-    const size_t per_cta = TMA_SMEM_LIMIT / (size_t)ctas - 1024;
-    long st = (long)(per_cta / tma_stage_bytes(c));
-    if (st > 8) st = 8;
-    return st >= 2 ? (int)st : 0;
+    const size_t budget = (ctas == 1 ? SMEM_PER_BLOCK_OPTIN : SMEM_PER_SM / (size_t)ctas - 1024) - 256;
+    int st = 0;
+    while (st < 8 && tma_smem_bytes(c, st + 1) <= budget) ++st;
+    return st >= 2 ? st : 0;
 }
 
 template <typename S, typename C, bool WALLS>
 static cudaError_t launch_tma(lbm_ctx* c, const S* src, S* dst, const FluidArgs& p) {
     const int stages = c->tma_stages;
-    const size_t smem = (((size_t)stages * tma_stage_bytes(c) + 15) & ~size_t(15)) + (size_t)stages * 8;
-    static size_t configured = 0;  // per instantiation: largest dynamic smem granted so far
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(fluid_step_tma_kernel<S, C, WALLS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM_LIMIT);
+    const size_t smem = tma_smem_bytes(c, stages);
+    static int max_dynamic = -1;  // per instantiation: opt-in minus the static shared memory
+    if (max_dynamic < 0) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, fluid_step_tma_kernel<S, C, WALLS>);
         if (e != cudaSuccess) return e;
-        configured = TMA_SMEM_LIMIT;
+        const int dyn = (int)SMEM_PER_BLOCK_OPTIN - (int)fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(fluid_step_tma_kernel<S, C, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dyn);
+        if (e != cudaSuccess) return e;
+        max_dynamic = dyn;
     }
+    if ((long)smem > (long)max_dynamic) return cudaErrorInvalidValue;
     const long rows = (long)c->box.ny * c->box.nz;
     long grid = (long)c->sms * c->tma_ctas;
     if (grid > rows) grid = rows;
     int block = ((c->box.nx + 31) / 32) * 32;
-    if (block > 512) block = 512;
+    if (block > 256) block = 256;
     fluid_step_tma_kernel<S, C, WALLS><<<(unsigned)grid, block, smem, c->stream>>>(src, dst, p, stages, c->status);
     return cudaSuccess;
 }
@@ -407,7 +415,7 @@ static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
         return cudaGetLastError();
     }
     const dim3 grid = step_grid(c->box, bx);
-    const bool pair = is16<S>() && (c->box.nx % 2 == 0);
+    const bool pair = is16<S>() && c->variant == 2 && (c->box.nx % 2 == 0);
     const dim3 grid2((unsigned)((c->box.nx / 2 + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)c->box.nz);
     for (long s = 0; s < n; ++s) {
         const S* src = (const S*)c->buf[c->cur];

@@ -154,8 +154,11 @@ float time_dry_steps(lbm_ctx* c, long reps, cudaError_t* err) {
 extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads, int stages, int ctas) {
     if (!c || c->batch || !c->owns) return LBM_ERR_ARG;
     if (threads < 32 || threads > 256 || threads % 32 != 0) return LBM_ERR_ARG;
-    if (variant == 0) {
-        c->variant = 0;
+    if (variant == 0 || variant == 2) {
+        if (variant == 2 && !(c->physics == LBM_PHYS_FLUID &&
+                              (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) && c->box.nx % 2 == 0))
+            return LBM_ERR_UNSUPPORTED;
+        c->variant = variant;
         c->block_x = threads;
         return LBM_OK;
     }
@@ -214,7 +217,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
                 c->tma_stages = stages;
                 c->tma_ctas = ctas;
             } else {
-                c->variant = 0;
+                c->variant = variant == 2 ? 2 : 0;
             }
         }
         if (mlups) *mlups = h.count("mlups") ? h["mlups"] : 0.0;
@@ -250,7 +253,10 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
         };
         std::vector<Cand> cands;
         for (int bx : {64, 128, 256}) cands.push_back({0, bx, 0, 1});
-        for (int ctas : {1, 2}) {
+        if (c->physics == LBM_PHYS_FLUID && (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) &&
+            c->box.nx % 2 == 0)
+            for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
+        for (int ctas : {1, 2, 3, 4}) {
             const int smax = lbm::fluid_tma_max_stages(c, ctas);
             for (int st : {2, 3, 4, 6, 8})
                 if (st <= smax) cands.push_back({1, c->block_x, st, ctas});

@@ -87,7 +87,7 @@ def test_16bit_two_cell_kernel(precision, shape, periodic):
     rho, u = inputs.random_fields(shape, seed=33, u_amp=0.03)
     kw = dict(periodic=periodic, lid_u=(0.05, 0.0, 0.01), g=(1e-5, 0.0, 0.0))
     o = oracle_run(shape, 1.4, 20, rho, u, **kw)
-    r = gpu_run(shape, 1.4, 20, rho, u, precision=precision, **kw)
+    r = gpu_run(shape, 1.4, 20, rho, u, precision=precision, launch=(2, 64, 0, 1), **kw)
     compare(r, o, TOL[precision])
 
 
