@@ -206,6 +206,46 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int force, double 
 lbm_status lbm_set_launch_shape(lbm_ctx *ctx, int variant, int threads, int stages, int ctas);
 lbm_status lbm_get_launch_shape(const lbm_ctx *ctx, int *variant, int *threads, int *stages, int *ctas);
 
+/* ---- Learned warm start ---------------------------------------------------
+ * A 3D convolutional network predicts the steady (rho, u) of the lid-driven
+ * cavity from the Reynolds number; lbm_cnn_warm_start initialises a solver
+ * with the prediction (populations at the equilibrium of the predicted
+ * fields) so that it iterates to the steady residual from there instead of
+ * from rest.  The network is an addition of this library (the paper has no
+ * learned component): 4 layers of 3x3x3 zero-padded convolutions,
+ * 5 -> 32 -> 32 -> 32 -> 4 channels, ReLU after the first three, BF16
+ * activations and kernel weights on the tensor cores, FP32 master weights,
+ * gradients and Adam moments.
+ * Inputs per node: (Re - 550)/450, the node-centre coordinates scaled to
+ * [-1, 1], and 1 on the top (+y, lid) layer of nodes.  Outputs per node:
+ * (rho - 1) * 30 and u * 10 (lid speed 0.1 -> 1).
+ * Parameters (lbm_cnn_param_count of them): per layer, weights
+ * [C_out][C_in][27] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)) then biases [C_out].
+ * Fields are FP64 planar ([n] rho, [3n] u), host or device pointers. */
+typedef struct lbm_cnn lbm_cnn;
+size_t lbm_cnn_param_count(void);
+/* init_weights: NULL = deterministic He-uniform initialisation. */
+lbm_status lbm_cnn_create(lbm_cnn **out, int nx, int ny, int nz, const float *init_weights, void *cuda_stream);
+void lbm_cnn_destroy(lbm_cnn *net);
+const char *lbm_cnn_last_error(const lbm_cnn *net);
+lbm_status lbm_cnn_set_weights(lbm_cnn *net, const float *w, size_t count);
+lbm_status lbm_cnn_get_weights(lbm_cnn *net, float *w, size_t count);
+/* Input channels from the Reynolds number (device-side). */
+lbm_status lbm_cnn_set_input(lbm_cnn *net, double reynolds);
+/* Input channels given explicitly: x [n][5] FP32 (tests). */
+lbm_status lbm_cnn_set_input_raw(lbm_cnn *net, const float *x, size_t count);
+/* Forward pass; out (optional) receives the [n][4] FP32 outputs. */
+lbm_status lbm_cnn_forward(lbm_cnn *net, float *out, size_t count);
+/* Loss (mean squared error of the 4 outputs against the scaled fields) and
+ * its gradient with respect to all parameters (grad_out optional). */
+lbm_status lbm_cnn_gradient(lbm_cnn *net, const double *rho, const double *u, double *loss, float *grad_out,
+                            size_t count);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the gradient of the
+ * loss against the given steady fields. */
+lbm_status lbm_cnn_train_step(lbm_cnn *net, const double *rho, const double *u, float lr, double *loss);
+/* Predict for `reynolds` and initialise ctx (same grid) from the prediction. */
+lbm_status lbm_cnn_warm_start(lbm_cnn *net, lbm_ctx *ctx, double reynolds);
+
 /* Allocation-free FP64 reduction of a single-phase population state that the
  * caller owns (the paper has no counterpart; it exists for callers that may
  * not allocate device memory: applications that own all device memory

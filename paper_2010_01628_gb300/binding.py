@@ -389,6 +389,109 @@ def lbm_autotune(ctx, cache_path=None, force=False):
     return m.value
 
 
+# --- learned warm start ------------------------------------------------------------
+_F = ctypes.POINTER(ctypes.c_float)
+_lib.lbm_cnn_param_count.restype = ctypes.c_size_t
+_lib.lbm_cnn_create.argtypes = [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int, ctypes.c_int, _V, _V]
+_lib.lbm_cnn_destroy.argtypes = [_V]
+_lib.lbm_cnn_destroy.restype = None
+_lib.lbm_cnn_last_error.argtypes = [_V]
+_lib.lbm_cnn_last_error.restype = ctypes.c_char_p
+_lib.lbm_cnn_set_weights.argtypes = [_V, _V, ctypes.c_size_t]
+_lib.lbm_cnn_get_weights.argtypes = [_V, _V, ctypes.c_size_t]
+_lib.lbm_cnn_set_input.argtypes = [_V, ctypes.c_double]
+_lib.lbm_cnn_set_input_raw.argtypes = [_V, _V, ctypes.c_size_t]
+_lib.lbm_cnn_forward.argtypes = [_V, _V, ctypes.c_size_t]
+_lib.lbm_cnn_gradient.argtypes = [_V, _V, _V, _D, _V, ctypes.c_size_t]
+_lib.lbm_cnn_train_step.argtypes = [_V, _V, _V, ctypes.c_float, _D]
+_lib.lbm_cnn_warm_start.argtypes = [_V, _V, ctypes.c_double]
+for _name in ("lbm_cnn_create", "lbm_cnn_set_weights", "lbm_cnn_get_weights", "lbm_cnn_set_input",
+              "lbm_cnn_set_input_raw", "lbm_cnn_forward", "lbm_cnn_gradient", "lbm_cnn_train_step",
+              "lbm_cnn_warm_start"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+def _check_cnn(status, net):
+    if status != LBM_OK:
+        raise LBMError(status, _lib.lbm_cnn_last_error(net).decode() if net else "")
+
+
+def _fptr(a, dtype):
+    if isinstance(a, np.ndarray):
+        assert a.dtype == dtype and a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def lbm_cnn_param_count():
+    return int(_lib.lbm_cnn_param_count())
+
+
+def lbm_cnn_create(shape, init_weights=None, stream=None):
+    """Network for grids of shape (nx, ny, nz); init_weights: float32 array or None."""
+    if _alloc_refs is None and _torch() is not None:
+        lbm_set_allocator(True)
+    net = _V()
+    w = None
+    if init_weights is not None:
+        w = np.ascontiguousarray(init_weights, dtype=np.float32)
+        assert w.size == lbm_cnn_param_count()
+    s = _current_stream() if stream is None else int(stream)
+    _check(_lib.lbm_cnn_create(ctypes.byref(net), *(int(v) for v in shape), _V(w.ctypes.data) if w is not None else None,
+                               _V(s)))
+    return net.value
+
+
+def lbm_cnn_destroy(net):
+    if net:
+        _lib.lbm_cnn_destroy(net)
+
+
+def lbm_cnn_set_weights(net, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    _check_cnn(_lib.lbm_cnn_set_weights(net, _V(w.ctypes.data), w.size), net)
+
+
+def lbm_cnn_get_weights(net):
+    w = np.empty(lbm_cnn_param_count(), dtype=np.float32)
+    _check_cnn(_lib.lbm_cnn_get_weights(net, _V(w.ctypes.data), w.size), net)
+    return w
+
+
+def lbm_cnn_set_input(net, reynolds):
+    _check_cnn(_lib.lbm_cnn_set_input(net, float(reynolds)), net)
+
+
+def lbm_cnn_set_input_raw(net, x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    _check_cnn(_lib.lbm_cnn_set_input_raw(net, _V(x.ctypes.data), x.size), net)
+
+
+def lbm_cnn_forward(net, n_nodes):
+    out = np.empty((n_nodes, 4), dtype=np.float32)
+    _check_cnn(_lib.lbm_cnn_forward(net, _V(out.ctypes.data), out.size), net)
+    return out
+
+
+def lbm_cnn_gradient(net, rho, u):
+    loss = ctypes.c_double()
+    g = np.empty(lbm_cnn_param_count(), dtype=np.float32)
+    _check_cnn(_lib.lbm_cnn_gradient(net, _V(_fptr(rho, np.float64)), _V(_fptr(u, np.float64)), ctypes.byref(loss),
+                                     _V(g.ctypes.data), g.size), net)
+    return loss.value, g
+
+
+def lbm_cnn_train_step(net, rho, u, lr):
+    loss = ctypes.c_double()
+    _check_cnn(_lib.lbm_cnn_train_step(net, _V(_fptr(rho, np.float64)), _V(_fptr(u, np.float64)), float(lr),
+                                       ctypes.byref(loss)), net)
+    return loss.value
+
+
+def lbm_cnn_warm_start(net, ctx, reynolds):
+    _check_cnn(_lib.lbm_cnn_warm_start(net, ctx, float(reynolds)), net)
+
+
 def lbm_destroy(ctx):
     if ctx:
         _lib.lbm_destroy(ctx)

@@ -127,6 +127,11 @@ lbm_status device_status(lbm_ctx* c) {
 }  // namespace
 
 void* lbm_internal_dev_alloc(lbm_ctx* c, size_t bytes) { return dev_alloc(c, bytes); }
+void lbm_internal_get_allocator(lbm_alloc_fn* a, lbm_free_fn* r, void** user) {
+    *a = g_alloc;
+    *r = g_release;
+    *user = g_user;
+}
 void lbm_internal_dev_free(lbm_ctx* c, void* p) { dev_free(c, p); }
 void lbm_internal_release(lbm_ctx* c) {
     if (c->batch) lbm_internal_free_batch_tables(c);

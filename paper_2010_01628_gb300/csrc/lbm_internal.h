@@ -50,6 +50,7 @@ struct lbm_ctx {
 
 // Helpers shared between the C-ABI translation units.
 void* lbm_internal_dev_alloc(lbm_ctx* c, size_t bytes);
+void lbm_internal_get_allocator(lbm_alloc_fn* a, lbm_free_fn* r, void** user);
 void lbm_internal_dev_free(lbm_ctx* c, void* p);
 lbm_status lbm_internal_alloc_batch(lbm_ctx* c, size_t state_elems, size_t cells, size_t max_plane);
 void lbm_internal_release(lbm_ctx* c);
