@@ -139,9 +139,10 @@ lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *phase, doubl
  * pointer may be NULL.  Synchronises. */
 lbm_status lbm_reduce(lbm_ctx *ctx, double *out_mass, double *out_mom, double *out_residual);
 
-/* Steady-state driver: steps until the one-step residual (lbm_reduce's
- * definition, evaluated every `check_every` steps) is <= tol, or until
- * max_steps.  Reports the steps taken and the last residual. */
+/* Steady-state driver: steps until the residual ||u^n - u^(n-k)||_2 /
+ * (k ||u^n||_2) over the check interval k = check_every (the mean per-step
+ * relative change, FP64 sums over all nodes) is <= tol, or until max_steps.
+ * Reports the steps taken and the last residual. */
 lbm_status lbm_run_to_steady(lbm_ctx *ctx, long max_steps, long check_every, double tol, long *steps_done,
                              double *residual);
 

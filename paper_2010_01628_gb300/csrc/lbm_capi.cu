@@ -426,25 +426,23 @@ lbm_status lbm_run_to_steady(lbm_ctx* c, long max_steps, long check_every, doubl
                              double* residual) {
     if (!c || max_steps < 0 || check_every < 1 || !(tol > 0)) return LBM_ERR_ARG;
     if (c->batch || !c->owns) return fail(c, LBM_ERR_UNSUPPORTED, "steady driver runs on single-domain contexts%s");
+    // residual = ||u^n - u^(n-k)|| / (k ||u^n||), k = check_every: the mean
+    // per-step rate of change over the check interval
     long done = 0;
     double res = -1.0;
-    lbm_status s = LBM_OK;
-    while (done < max_steps) {
-        long chunk = check_every - 1;
-        if (done + chunk + 1 > max_steps) chunk = max_steps - done - 1;
-        if (chunk > 0) {
-            s = lbm_step(c, chunk);
-            if (s != LBM_OK) break;
-            done += chunk;
-        }
-        s = lbm_reduce(c, nullptr, nullptr, nullptr);  // records u(n-1)
+    c->have_prev = false;
+    lbm_status s = lbm_reduce(c, nullptr, nullptr, nullptr);  // records u at the start
+    while (s == LBM_OK && done < max_steps) {
+        long k = check_every;
+        if (done + k > max_steps) k = max_steps - done;
+        s = lbm_step(c, k);
         if (s != LBM_OK) break;
-        s = lbm_step(c, 1);
+        done += k;
+        double r = -1.0;
+        s = lbm_reduce(c, nullptr, nullptr, &r);  // compares with the previous check, records u
         if (s != LBM_OK) break;
-        done += 1;
-        s = lbm_reduce(c, nullptr, nullptr, &res);  // one-step residual at n
-        c->have_prev = false;
-        if (s != LBM_OK || res <= tol) break;
+        res = r / (double)k;
+        if (res <= tol) break;
     }
     if (steps_done) *steps_done = done;
     if (residual) *residual = res;

@@ -1,7 +1,8 @@
 """Learned warm start for the lid-driven cavity (orchestration over the C ABI).
 
-1. Steady states: the solver (FP32 storage) runs each cavity to a one-step
-   velocity residual ||u^n - u^(n-1)|| / ||u^n|| <= tol (lbm_run_to_steady).
+1. Steady states: the solver (FP32 storage) runs each cavity until the mean
+   per-step velocity change over the check interval k,
+   ||u^n - u^(n-k)|| / (k ||u^n||), is <= tol (lbm_run_to_steady).
    With ``continuation`` the Reynolds numbers are visited in increasing order
    and each run starts from the previous steady state (faster data generation;
    the targets are still the converged states).
@@ -41,8 +42,11 @@ def _cavity(n, reynolds, precision="fp32"):
                         precision=precision)
 
 
-def steady_states(n, re_list, tol=1e-6, check_every=100, max_steps=3_000_000, continuation=True, precision="fp32",
+def steady_states(n, re_list, tol=1e-6, check_every=100, max_steps=400_000, continuation=True, precision="fp32",
                   log=None):
+    """Converged steady states (dicts with re, rho, u on the GPU, steps,
+    residual, seconds), in increasing Re.  Runs that do not reach `tol` within
+    `max_steps` are reported with ``converged`` False; the caller decides."""
     import torch
     out = []
     prev = None
@@ -60,8 +64,10 @@ def steady_states(n, re_list, tol=1e-6, check_every=100, max_steps=3_000_000, co
             L.lbm_fields(ctx, (n, n, n), rho=rho, u=u)
         finally:
             L.lbm_destroy(ctx)
-        prev = (rho, u)
-        out.append({"re": re, "rho": rho, "u": u, "steps": steps, "residual": res, "seconds": dt})
+        ok = 0 <= res <= tol
+        if ok:
+            prev = (rho, u)
+        out.append({"re": re, "rho": rho, "u": u, "steps": steps, "residual": res, "seconds": dt, "converged": ok})
         if log:
             log(f"steady Re={re:7.1f} steps={steps} residual={res:.2e} {dt:.2f}s")
     return out
@@ -101,7 +107,7 @@ def _run(n, re, tol, check_every, max_steps, net=None):
     return steps, res, dt
 
 
-def evaluate(net, n, re_list, tol=1e-6, check_every=100, max_steps=3_000_000, log=None):
+def evaluate(net, n, re_list, tol=1e-6, check_every=100, max_steps=400_000, log=None):
     cases = []
     for re in re_list:
         cs, cr, ct = _run(n, float(re), tol, check_every, max_steps)
@@ -127,6 +133,7 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--max-steps", type=int, default=400_000)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     import torch
@@ -138,18 +145,20 @@ def main():
     res = inputs.cavity_reynolds(args.train + args.heldout, seed=4)
     train_re, held_re = res[:args.train], res[args.train:]
     t0 = time.perf_counter()
-    data = steady_states(args.n, train_re, args.tol, args.check_every, log=log)
+    all_states = steady_states(args.n, train_re, args.tol, args.check_every, max_steps=args.max_steps, log=log)
+    data = [d for d in all_states if d["converged"]]
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     net = train(args.n, data, args.epochs, args.lr, log=log)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    rep = evaluate(net, args.n, held_re, args.tol, args.check_every, log=log)
+    rep = evaluate(net, args.n, held_re, args.tol, args.check_every, max_steps=args.max_steps, log=log)
     L.lbm_cnn_destroy(net)
     rep.update({"grid": args.n, "train_states": len(data), "heldout": len(held_re), "epochs": args.epochs,
                 "lr": args.lr, "tol": args.tol, "check_every": args.check_every,
                 "data_generation_s": t_data, "training_s": t_train, "loss_history": train.history,
-                "data_steps_total": int(sum(d["steps"] for d in data))})
+                "data_steps_total": int(sum(d["steps"] for d in all_states)),
+                "unconverged_training_states": [d["re"] for d in all_states if not d["converged"]]})
     txt = json.dumps(rep, indent=1)
     if args.out:
         with open(args.out, "w") as fh:
