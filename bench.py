@@ -350,6 +350,10 @@ def run_ours(args):
 
     n, prec = args.n, args.precision
     stream = torch.cuda.current_stream()
+    if args.only == "fma-probe":
+        f64, f32 = L.lbm_probe_fma_rate()
+        print(json.dumps({"only": "fma-probe", "fp64_fma_per_s": f64, "fp32_fma_per_s": f32}), flush=True)
+        return 0
     if args.only:
         peak, _ = measured_peaks()
         res = extra_workloads(L, torch, stream, args.steps, peak, only=args.only, domains=args.domains,
@@ -462,7 +466,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm"], default=None,
+    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "fma-probe"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     ap.add_argument("--launch", default="auto",

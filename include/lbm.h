@@ -247,6 +247,11 @@ lbm_status lbm_cnn_train_step(lbm_cnn *net, const double *rho, const double *u, 
 /* Predict for `reynolds` and initialise ctx (same grid) from the prediction. */
 lbm_status lbm_cnn_warm_start(lbm_cnn *net, lbm_ctx *ctx, double reynolds);
 
+/* Measured FMA throughput of the current device (independent FMA chains, best
+ * of 3): FP64 and FP32 fused multiply-adds per second.  The FP64 step is
+ * bound by the FP64 pipe; this is the denominator of its ALU roofline. */
+lbm_status lbm_probe_fma_rate(double *fp64_fma_per_s, double *fp32_fma_per_s);
+
 /* Allocation-free FP64 reduction of a single-phase population state that the
  * caller owns (the paper has no counterpart; it exists for callers that may
  * not allocate device memory: applications that own all device memory

@@ -492,6 +492,16 @@ def lbm_cnn_warm_start(net, ctx, reynolds):
     _check_cnn(_lib.lbm_cnn_warm_start(net, ctx, float(reynolds)), net)
 
 
+_lib.lbm_probe_fma_rate.argtypes = [_D, _D]
+_lib.lbm_probe_fma_rate.restype = ctypes.c_int
+
+
+def lbm_probe_fma_rate():
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.lbm_probe_fma_rate(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def lbm_destroy(ctx):
     if ctx:
         _lib.lbm_destroy(ctx)
