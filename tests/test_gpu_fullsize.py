@@ -1,0 +1,95 @@
+"""Parity at the full workload sizes, in the launch configurations the
+benchmark times: the 64-domain Hartmann batch (one persistent graph-captured
+launch per call, autotuned shape) and the 256^3 colour-gradient droplets.
+Outputs are checked on sampled domains or nodes the oracle can compute alone.
+"""
+import numpy as np
+import pytest
+
+from helpers import oracle_run, rel_l2
+from paper_2010_01628_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mhd_batch_64_domains_sampled():
+    from paper_2010_01628_gb300 import binding as L
+    sweep = inputs.hartmann_batch(64, seed=2)
+    nu = 0.1
+    omega = 1 / (nu / (1 / 3) + 0.5)
+    tau_m = 0.5 + nu / 0.25
+    shapes = [(n, n, n) for n, _ in sweep]
+    b0s = [2 * ha * nu / n for n, ha in sweep]
+    gs = [(8 * nu * 0.01 / n ** 2, 0.0, 0.0) for n, _ in sweep]
+    batch = L.lbm_batch_create(shapes, omega, periodic=(True, False, True), physics="mhd", precision="fp32",
+                               tau_m=tau_m, g=gs, b_wall=[(0.0, b, 0.0) for b in b0s])
+    steps = 5
+    # smallest domain of each size is compared in full
+    pick = {}
+    for k, (n, _) in enumerate(sweep):
+        pick.setdefault(n, k)
+    init = {}
+    try:
+        for k, (n, _) in enumerate(sweep):
+            rho, u = inputs.random_fields((n, n, n), seed=100 + k, u_amp=0.01)
+            B = np.zeros((3, n, n, n))
+            B[1] = b0s[k]
+            if k in pick.values():
+                init[k] = (rho, u, B)
+            L.lbm_init_fields(L.lbm_batch_domain(batch, k), rho, u, B=B)
+        L.lbm_autotune(batch, None)
+        L.lbm_batch_step(batch, 2)
+        L.lbm_batch_step(batch, 3)
+        L.lbm_sync(batch)
+        outs = {k: L.lbm_fields(L.lbm_batch_domain(batch, k), shapes[k], want=("rho", "u", "B")) for k in init}
+    finally:
+        L.lbm_destroy(batch)
+    for k, (rho, u, B) in init.items():
+        o = oracle_run(shapes[k], omega, steps, rho, u, B=B, physics="mhd", periodic=(True, False, True), g=gs[k],
+                       b_wall=(0.0, b0s[k], 0.0), tau_m=tau_m, threads=None)
+        for f in ("rho", "u", "B"):
+            assert rel_l2(outs[k][f], o[f]) <= 1e-5, (shapes[k], f)
+
+
+def test_cgm_droplets_256_sampled():
+    """256^3 droplets, FP32, 3 steps: nodes sampled inside, outside and on the
+    interfaces against the oracle run on their dependency cone (radius 2 per
+    step, +1 for the reported fields' gather)."""
+    from paper_2010_01628_gb300 import binding as L
+    n, k = 256, 3
+    rho, u, phase, spheres, _ = inputs.droplets(n, seed=3)
+    u = u + inputs.noise_box((n, n, n), amp=1e-2, seed=7)[1]
+    sigma, tau = 1e-4, 0.8
+    alpha_b = 1 / 3
+    alpha_r = 1 - (1 - alpha_b) / 10.0
+    kw = dict(alpha_r=alpha_r, alpha_b=alpha_b, A=9 * sigma / tau / 4, beta=0.7)
+    ctx = L.lbm_create((n, n, n), 1 / tau, physics="cgm", precision="fp32", **kw)
+    try:
+        L.lbm_init_fields(ctx, rho, u, phase=phase)
+        L.lbm_step(ctx, k)
+        out = L.lbm_fields(ctx, (n, n, n), want=("rho", "u", "phase"))
+    finally:
+        L.lbm_destroy(ctx)
+    r = 2 * k + 1
+    rng = np.random.default_rng(11)
+    centres = [(0, 0, 0), (n - 1, 5, n - 1)]
+    for (c, rad) in spheres[:4]:  # centre of a droplet and a point on its interface
+        ci = [int(round(v)) % n for v in c]
+        centres.append(tuple(ci))
+        centres.append(((ci[0] + int(round(rad))) % n, ci[1], ci[2]))
+    centres += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(4)]
+    got, ref = {"rho": [], "u": [], "phase": []}, {"rho": [], "u": [], "phase": []}
+    for (x, y, z) in centres:
+        idx = [(np.arange(-r, r + 1) + c) % n for c in (x, y, z)]
+        sub = lambda a: np.ascontiguousarray(a[np.ix_(idx[2], idx[1], idx[0])])
+        su = np.ascontiguousarray(u[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]])
+        L_ = 2 * r + 1
+        o = oracle_run((L_, L_, L_), 1 / tau, k, sub(rho), su, phase=sub(phase), physics="cgm", **kw)
+        got["rho"].append(out["rho"][z, y, x])
+        ref["rho"].append(o["rho"][r, r, r])
+        got["u"].append(out["u"][:, z, y, x])
+        ref["u"].append(o["u"][:, r, r, r])
+        got["phase"].append(out["phase"][z, y, x])
+        ref["phase"].append(o["phase"][r, r, r])
+    for f in ("rho", "u", "phase"):
+        assert rel_l2(got[f], ref[f]) <= 1e-5, f
