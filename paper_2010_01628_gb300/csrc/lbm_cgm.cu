@@ -46,7 +46,7 @@ __device__ __forceinline__ CgmNode<C> cgm_macro(const C (&fr)[Q], const C (&fb)[
     s.Fx = s.rho * (C)p.g[0];
     s.Fy = s.rho * (C)p.g[1];
     s.Fz = s.rho * (C)p.g[2];
-    const C inv = (C)1 / s.rho;
+    const C inv = recip(s.rho);
     s.ux = (m.jx + (C)0.5 * s.Fx) * inv;
     s.uy = (m.jy + (C)0.5 * s.Fy) * inv;
     s.uz = (m.jz + (C)0.5 * s.Fz) * inv;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ 
     const C pert_amp = (C)0.5 * (C)p.A * nrm;
     const C inv_n2 = n2 > (C)1e-24 ? (C)1 / n2 : (C)0;
     const C inv_nrm = nrm > (C)1e-12 ? (C)1 / nrm : (C)0;
-    const C inv_rho = (C)1 / s.rho;
+    const C inv_rho = recip(s.rho);
     const C frac_r = s.rho_r * inv_rho, frac_b = s.rho_b * inv_rho;
     // beta rho_r rho_b / rho^2 * g_eq(rho, 0) with g_eq = rho phi_i(alpha)
     const C sep = (C)p.beta * s.rho_r * s.rho_b * inv_rho;

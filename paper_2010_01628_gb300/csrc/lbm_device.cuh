@@ -196,8 +196,8 @@ __device__ __forceinline__ Moments<C> moments19(const C (&f)[Q]) {
     m.jz = sz_p - sz_m;
     // sum_i f c_a^2: directions with c_a != 0 are exactly those counted above
     const C pxx = sx_p + sx_m, pyy = sy_p + sy_m, pzz = sz_p + sz_m;
-    m.drho = f[0] + (f[1] + f[10]) + (f[2] + f[11]) + (f[3] + f[12]) + (f[4] + f[13]) + (f[5] + f[14]) +
-             (f[6] + f[15]) + (f[7] + f[16]) + (f[8] + f[17]) + (f[9] + f[18]);
+    // c_x = 0 directions: 0, 2, 3, 8, 9, 11, 12, 17, 18
+    m.drho = pxx + f[0] + (f[2] + f[11]) + (f[3] + f[12]) + (f[8] + f[17]) + (f[9] + f[18]);
     m.pxx_m_pyy = pxx - pyy;
     m.pyy_m_pzz = pyy - pzz;
     m.pxy = (f[4] + f[13]) - (f[5] + f[14]);
@@ -239,20 +239,22 @@ __device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C 
     r[7] = rho * ux * uy + uy * hx + ux * hy + k7;
     r[8] = rho * ux * uz + uz * hx + ux * hz + k8;
     r[9] = rho * uy * uz + uz * hy + uy * hz + k9;
-    // third order: sum f c_a^2 c_b = k(a^2 b) + u_b Xa + 2 u_a k(ab) + 2 u_a u_b h_a + u_a^2 h_b + rho u_a^2 u_b
-    r[10] = rho * x2 * uy + (C)2 * ux * uy * hx + x2 * hy + uy * Xs + (C)2 * ux * k7 + t[0];
-    r[11] = rho * ux * y2 + y2 * hx + (C)2 * ux * uy * hy + ux * Ys + (C)2 * uy * k7 + t[1];
-    r[12] = rho * x2 * uz + (C)2 * ux * uz * hx + x2 * hz + uz * Xs + (C)2 * ux * k8 + t[2];
-    r[13] = rho * ux * z2 + z2 * hx + (C)2 * ux * uz * hz + ux * Zs + (C)2 * uz * k8 + t[3];
-    r[14] = rho * y2 * uz + (C)2 * uy * uz * hy + y2 * hz + uz * Ys + (C)2 * uy * k9 + t[4];
-    r[15] = rho * uy * z2 + z2 * hy + (C)2 * uy * uz * hz + uy * Zs + (C)2 * uz * k9 + t[5];
-    // fourth order: sum f c_a^2 c_b^2
-    r[16] = rho * x2 * y2 + (C)2 * ux * y2 * hx + (C)2 * x2 * uy * hy + y2 * Xs + x2 * Ys + (C)4 * ux * uy * k7 +
-            (C)2 * uy * t[0] + (C)2 * ux * t[1] + k16c;
-    r[17] = rho * x2 * z2 + (C)2 * ux * z2 * hx + (C)2 * x2 * uz * hz + z2 * Xs + x2 * Zs + (C)4 * ux * uz * k8 +
-            (C)2 * uz * t[2] + (C)2 * ux * t[3] + k17c;
-    r[18] = rho * y2 * z2 + (C)2 * uy * z2 * hy + (C)2 * y2 * uz * hz + z2 * Ys + y2 * Zs + (C)4 * uy * uz * k9 +
-            (C)2 * uz * t[4] + (C)2 * uy * t[5] + k18c;
+    // third order: sum f c_a^2 c_b = k(a^2 b) + u_b Xa + 2 u_a k(ab) + 2 u_a u_b h_a + u_a^2 h_b + rho u_a^2 u_b,
+    // grouped as u_a^2 (rho u_b + h_b) + u_b (2 u_a h_a + Xa) + 2 u_a k(ab) + k(a^2 b)
+    const C Ax = (C)2 * ux * hx + Xs, Ay = (C)2 * uy * hy + Ys, Az = (C)2 * uz * hz + Zs;
+    const C tx = (C)2 * ux, ty = (C)2 * uy, tz = (C)2 * uz;
+    r[10] = x2 * r[2] + uy * Ax + tx * k7 + t[0];
+    r[11] = y2 * r[1] + ux * Ay + ty * k7 + t[1];
+    r[12] = x2 * r[3] + uz * Ax + tx * k8 + t[2];
+    r[13] = z2 * r[1] + ux * Az + tz * k8 + t[3];
+    r[14] = y2 * r[3] + uz * Ay + ty * k9 + t[4];
+    r[15] = z2 * r[2] + uy * Az + tz * k9 + t[5];
+    // fourth order: sum f c_a^2 c_b^2 = u_b^2 (rho u_a^2 + A_a) + u_a^2 A_b + 2 u_a (2 u_b k(ab) + k(a b^2))
+    //                                   + 2 u_b k(a^2 b) + k(a^2 b^2)
+    const C rx2 = rho * x2, ry2 = rho * y2;
+    r[16] = y2 * (rx2 + Ax) + x2 * Ay + tx * (ty * k7 + t[1]) + ty * t[0] + k16c;
+    r[17] = z2 * (rx2 + Ax) + x2 * Az + tx * (tz * k8 + t[3]) + tz * t[2] + k17c;
+    r[18] = z2 * (ry2 + Ay) + y2 * Az + ty * (tz * k9 + t[5]) + tz * t[4] + k18c;
 
     const C half = (C)0.5, quarter = (C)0.25, sixth = (C)(1.0 / 6.0);
     const C ax = (r[4] + (C)2 * r[5] + r[6]) * sixth;
@@ -280,6 +282,10 @@ __device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C 
     f[17] = (r[9] + r[14] + r[15] + r[18]) * quarter;
     f[18] = (r[15] + r[18] - r[9] - r[14]) * quarter;
 }
+
+// 1/x: correctly rounded reciprocal (the FP32 division would add a slow path).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Macroscopic state of a gathered node: rho, F, u = (sum f c + F/2)/rho.
 template <typename C>

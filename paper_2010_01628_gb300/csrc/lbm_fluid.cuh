@@ -20,7 +20,7 @@ __device__ __forceinline__ Macro<C> fluid_macro(const Moments<C>& m, C gx, C gy,
     a.Fx = a.rho * gx;  // F = rho g
     a.Fy = a.rho * gy;
     a.Fz = a.rho * gz;
-    const C inv = (C)1 / a.rho;
+    const C inv = recip(a.rho);
     a.ux = (m.jx + (C)0.5 * a.Fx) * inv;
     a.uy = (m.jy + (C)0.5 * a.Fy) * inv;
     a.uz = (m.jz + (C)0.5 * a.Fz) * inv;

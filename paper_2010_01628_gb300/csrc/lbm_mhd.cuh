@@ -68,7 +68,7 @@ template <typename C>
 __device__ __forceinline__ Macro<C> mhd_macro(const Moments<C>& m, const C (&g)[7][3], const MhdArgs& p, C (&bb)[3]) {
     Macro<C> a;
     a.rho = (C)1 + m.drho;
-    const C inv = (C)1 / a.rho;
+    const C inv = recip(a.rho);
     const C us[3] = {m.jx * inv, m.jy * inv, m.jz * inv};
 #pragma unroll
     for (int k = 0; k < 3; ++k) bb[k] = g[0][k] + g[1][k] + g[2][k] + g[3][k] + g[4][k] + g[5][k] + g[6][k];
