@@ -27,7 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 Q = 19
-FLUID, MHD, CGM = 0, 1, 2
+FLUID, MHD, CGM, SC = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -74,6 +74,7 @@ def _load():
             lib.orc_init.argtypes = [PP, P, P, P, P, P, P, P, P]
             lib.orc_step.argtypes = [PP, P, P, P, P, P, P, P, P, P, ctypes.c_long]
             lib.orc_fields.argtypes = [PP, P, P, P, P, P, P, P, P]
+            lib.orc_sc_force_field.argtypes = [PP, P, P]
             _lib = lib
     return _lib
 
@@ -233,7 +234,8 @@ class _Params(ctypes.Structure):
                 ("g", ctypes.c_double * 3), ("physics", ctypes.c_int), ("closed_form", ctypes.c_int),
                 ("tau_m", ctypes.c_double), ("b_wall", ctypes.c_double * 3),
                 ("alpha_r", ctypes.c_double), ("alpha_b", ctypes.c_double),
-                ("A", ctypes.c_double), ("beta", ctypes.c_double), ("nthreads", ctypes.c_int)]
+                ("A", ctypes.c_double), ("beta", ctypes.c_double), ("nthreads", ctypes.c_int),
+                ("G", ctypes.c_double)]
 
 
 class Domain:
@@ -246,7 +248,7 @@ class Domain:
 
     def __init__(self, shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                  physics=FLUID, closed_form=True, omega_b=1.0, omega_3=1.0, omega_4=1.0, tau_m=1.0,
-                 b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7):
+                 b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz
@@ -262,12 +264,14 @@ class Domain:
         p.closed_form = int(bool(closed_form))
         p.tau_m = float(tau_m)
         p.alpha_r, p.alpha_b, p.A, p.beta = map(float, (alpha_r, alpha_b, A, beta))
+        p.G = float(G)
         self.p = p
         self.physics = physics
         n = self.n
         z = lambda k: np.zeros(n * k, dtype=np.float64)
         self.f = z(Q)
         self.ftmp = z(Q) if physics != CGM else None
+        self.psi = z(1) if physics == SC else None
         self.g = z(21) if physics == MHD else None
         self.gtmp = z(21) if physics == MHD else None
         if physics == CGM:
@@ -293,7 +297,8 @@ class Domain:
 
     def step(self, n=1):
         rc = _load().orc_step(ctypes.byref(self.p), _p(self.f), _p(self.ftmp), _p(self.g), _p(self.gtmp),
-                              _p(self.fr), _p(self.fb), _p(self.frtmp), _p(self.fbtmp), _p(self.phi), int(n))
+                              _p(self.fr), _p(self.fb), _p(self.frtmp), _p(self.fbtmp),
+                              _p(self.psi if self.physics == SC else self.phi), int(n))
         if rc != 0:
             raise RuntimeError("oracle: singular moment matrix")
 
@@ -302,13 +307,22 @@ class Domain:
         nx, ny, nz = self.shape
         rho = np.zeros(self.n)
         u = np.zeros(3 * self.n)
-        phase = np.zeros(self.n) if self.physics == CGM else None
+        phase = np.zeros(self.n) if self.physics in (CGM, SC) else None
         B = np.zeros(3 * self.n) if self.physics == MHD else None
         _load().orc_fields(ctypes.byref(self.p), _p(self.f), _p(self.g), _p(self.fr), _p(self.fb), _p(rho), _p(u),
                            _p(phase), _p(B))
         shp = (nz, ny, nx)
         return (rho.reshape(shp), u.reshape((3,) + shp), None if phase is None else phase.reshape(shp),
                 None if B is None else B.reshape((3,) + shp))
+
+    def sc_force(self, psi):
+        """Shan-Chen force [3, nz, ny, nx] of a pseudopotential field psi [nz, ny, nx]
+        on this machine (walls as configured)."""
+        nx, ny, nz = self.shape
+        psi = self._field(psi)
+        F = np.zeros(3 * self.n)
+        _load().orc_sc_force_field(ctypes.byref(self.p), _p(psi), _p(F))
+        return F.reshape((3, nz, ny, nx))
 
     # populations in the oracle's cell-major layout [cell, 19]
     def populations(self):

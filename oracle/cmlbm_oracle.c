@@ -31,6 +31,11 @@
  * fields.  Reported fields are the moments of the gathered (post-stream)
  * populations, with +F/2 in the momentum (App. E, macroscopic variables).
  *
+ * Shan-Chen multiphase (Sec. III.G, physics 3) takes two passes per step:
+ * the pseudopotential psi = 1 - exp(-rho) of every node from its gathered
+ * densities, then the single-phase collision with F = rho g + F_sc, where
+ * F_sc = -G psi(x) sum_i w_i c_i psi(x + c_i).
+ *
  * Populations are stored cell-major: f[cell*19 + i], cell = x + nx*(y + ny*z).
  */
 #include <math.h>
@@ -508,12 +513,13 @@ typedef struct {
     double lid_u[3]; /* velocity of the +y wall (Ladd's moving-wall term, rho_w = 1) */
     double omega, omega_b, omega_3, omega_4;
     double g[3];     /* body acceleration, F = rho g */
-    int physics;     /* 0 single phase, 1 MHD, 2 colour gradient */
+    int physics;     /* 0 single phase, 1 MHD, 2 colour gradient, 3 Shan-Chen */
     int closed_form; /* 0: Oracle-A (dense), 1: Oracle-B (two-step closed form) */
     double tau_m;    /* MHD: magnetic relaxation time */
     double b_wall[3];
     double alpha_r, alpha_b, A, beta; /* CGM */
     int nthreads;
+    double G; /* Shan-Chen interaction strength (physics 3) */
 } orc_params;
 
 static long cell_index(const orc_params *p, int x, int y, int z)
@@ -606,11 +612,53 @@ int orc_max_threads(void)
 #endif
 }
 
+/* Sec. III.G: Shan-Chen pseudopotential psi = 1 - exp(-rho) and interaction
+ * force F(x) = -G psi(x) sum_i w_i c_i psi(x + c_i) (no c_s^2 factor, as
+ * printed).  psi holds the pseudopotential of every node computed from the
+ * post-stream densities; a neighbour behind a wall contributes the node's own
+ * psi. */
+static void sc_force(const orc_params *p, const double *psi, int x, int y, int z, double *F)
+{
+    double own = psi[cell_index(p, x, y, z)];
+    double sx = 0, sy = 0, sz = 0;
+    for (int i = 1; i < Q; i++) {
+        int nx_ = wrap(x + CX[i], p->nx, p->periodic[0]);
+        int ny_ = wrap(y + CY[i], p->ny, p->periodic[1]);
+        int nz_ = wrap(z + CZ[i], p->nz, p->periodic[2]);
+        double v = (nx_ >= 0 && ny_ >= 0 && nz_ >= 0) ? psi[cell_index(p, nx_, ny_, nz_)] : own;
+        sx += weight(i) * CX[i] * v;
+        sy += weight(i) * CY[i] * v;
+        sz += weight(i) * CZ[i] * v;
+    }
+    F[0] = -p->G * own * sx;
+    F[1] = -p->G * own * sy;
+    F[2] = -p->G * own * sz;
+}
+
+/* The Shan-Chen force of every node for a given pseudopotential field psi
+ * (layout [nz][ny][nx]); F is [3][nz][ny][nx]. */
+void orc_sc_force_field(const orc_params *p, const double *psi, double *F)
+{
+    long n = (long)p->nx * p->ny * p->nz;
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                long c = cell_index(p, x, y, z);
+                double Fc[3];
+                sc_force(p, psi, x, y, z, Fc);
+                F[c] = Fc[0];
+                F[n + c] = Fc[1];
+                F[2 * n + c] = Fc[2];
+            }
+}
+
 /* Per-node macroscopic state of a gathered set, shared by step and fields. */
 typedef struct {
     double rho, u[3], F[3], b[3], j[3];
 } node_state;
 
+static void node_macro_sc(const orc_params *p, const double *fin, const double *gin, const double *psi, int x, int y,
+                          int z, node_state *s);
 static void node_macro(const orc_params *p, const double *fin, const double *gin, node_state *s)
 {
     double jx, jy, jz;
@@ -644,6 +692,38 @@ static int collide(const orc_params *p, const double *fin, const node_state *s, 
                                   alpha, fout);
     return orc_collide_dense(fin, s->rho, s->u[0], s->u[1], s->u[2], s->F[0], s->F[1], s->F[2], p->omega,
                              p->omega_b, p->omega_3, p->omega_4, cgm, alpha, fout);
+}
+
+/* Macroscopic state with the Shan-Chen force added to the body force. */
+static void node_macro_sc(const orc_params *p, const double *fin, const double *gin, const double *psi, int x, int y,
+                          int z, node_state *s)
+{
+    double jx, jy, jz, Fsc[3];
+    (void)gin;
+    raw_moments(fin, &s->rho, &jx, &jy, &jz);
+    sc_force(p, psi, x, y, z, Fsc);
+    for (int a = 0; a < 3; a++) {
+        s->F[a] = s->rho * p->g[a] + Fsc[a];
+        s->b[a] = s->j[a] = 0.0;
+    }
+    s->u[0] = (jx + 0.5 * s->F[0]) / s->rho;
+    s->u[1] = (jy + 0.5 * s->F[1]) / s->rho;
+    s->u[2] = (jz + 0.5 * s->F[2]) / s->rho;
+}
+
+/* Pseudopotential of every node from the gathered (post-stream) densities. */
+static void sc_pseudopotential(const orc_params *p, const double *f, double *psi)
+{
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                double fin[Q], rho = 0;
+                gather_f(p, f, x, y, z, fin, 1);
+                for (int i = 0; i < Q; i++) rho += fin[i];
+                psi[cell_index(p, x, y, z)] = 1.0 - exp(-rho);
+            }
 }
 
 /* Initial state: populations at the equilibrium of the given fields (Sec.
@@ -779,6 +859,7 @@ int orc_step(const orc_params *p, double *f, double *ftmp, double *g, double *gt
             memcpy(fb, fbtmp, sizeof(double) * n * Q);
             continue;
         }
+        if (p->physics == 3) sc_pseudopotential(p, f, phi);
 #pragma omp parallel for schedule(static) reduction(| : err)
         for (int z = 0; z < nz; z++)
             for (int y = 0; y < ny; y++)
@@ -787,6 +868,11 @@ int orc_step(const orc_params *p, double *f, double *ftmp, double *g, double *gt
                     double fin[Q], gin[21];
                     node_state st;
                     gather_f(p, f, x, y, z, fin, 1);
+                    if (p->physics == 3) {
+                        node_macro_sc(p, fin, NULL, phi, x, y, z, &st);
+                        err |= collide(p, fin, &st, 0, 0.0, ftmp + c * Q) != 0;
+                        continue;
+                    }
                     if (p->physics == 1) gather_g(p, g, x, y, z, gin);
                     node_macro(p, fin, p->physics == 1 ? gin : NULL, &st);
                     err |= collide(p, fin, &st, 0, 0.0, ftmp + c * Q) != 0;
@@ -810,6 +896,12 @@ int orc_fields(const orc_params *p, const double *f, const double *g, const doub
 {
     int nx = p->nx, ny = p->ny, nz = p->nz;
     long n = (long)nx * ny * nz;
+    double *psi = NULL;
+    if (p->physics == 3) {
+        psi = (double *)malloc(sizeof(double) * n);
+        if (!psi) return -1;
+        sc_pseudopotential(p, f, psi);
+    }
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; z++)
         for (int y = 0; y < ny; y++)
@@ -828,6 +920,10 @@ int orc_fields(const orc_params *p, const double *f, const double *g, const doub
                     }
                     if (phase) phase[c] = (rr - rb) / (rr + rb);
                     node_macro(p, fin, NULL, &st);
+                } else if (p->physics == 3) {
+                    gather_f(p, f, x, y, z, fin, 1);
+                    node_macro_sc(p, fin, NULL, psi, x, y, z, &st);
+                    if (phase) phase[c] = psi[c];
                 } else {
                     gather_f(p, f, x, y, z, fin, 1);
                     if (p->physics == 1) gather_g(p, g, x, y, z, gin);
@@ -845,5 +941,6 @@ int orc_fields(const orc_params *p, const double *f, const double *g, const doub
                     u[2 * n + c] = st.u[2];
                 }
             }
+    free(psi);
     return 0;
 }
