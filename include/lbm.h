@@ -63,7 +63,8 @@ typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_SHIFTED = 2, LBM_BF16_SHIFTE
 typedef enum {
     LBM_PHYS_FLUID = 0, /* single phase, body force F = rho g (Sec. II)           */
     LBM_PHYS_MHD = 1,   /* + D3Q7 magnetic populations, F = j x b (Sec. III.F)    */
-    LBM_PHYS_CGM = 2    /* colour-gradient two-phase (App. E)                     */
+    LBM_PHYS_CGM = 2,   /* colour-gradient two-phase (App. E)                     */
+    LBM_PHYS_SC = 3     /* Shan-Chen pseudopotential multiphase (Sec. III.G)      */
 } lbm_physics;
 
 /* Box geometry.  A periodic axis wraps; a non-periodic axis has half-way
@@ -95,11 +96,16 @@ typedef struct {
  *   walls (anti-bounce-back).
  * CGM (App. E): alpha_r, alpha_b set phi_i(alpha) and the density ratio
  *   rho_r0/rho_b0 = (1 - alpha_b)/(1 - alpha_r); A is the perturbation
- *   amplitude (sigma = (4/9) A / omega); beta the recolouring parameter. */
+ *   amplitude (sigma = (4/9) A / omega); beta the recolouring parameter.
+ * Shan-Chen (Sec. III.G): G is the interaction strength of the force
+ *   F = -G psi(x) sum_i w_i c_i psi(x + c_i), psi = 1 - exp(-rho) (the static
+ *   bubble uses G = -5); a neighbour behind a wall contributes the node's own
+ *   psi. */
 typedef struct {
     double tau_m;
     double b_wall[3];
     double alpha_r, alpha_b, A, beta;
+    double G;
 } lbm_physparams;
 
 /* Device-memory provider.  alloc returns a device pointer of at least `bytes`
@@ -128,7 +134,8 @@ lbm_status lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u, con
 lbm_status lbm_step(lbm_ctx *ctx, long n);
 
 /* Macroscopic fields of the current state (any pointer may be NULL = skip):
- * rho [n]; u [3n] (with +F/2); phase [n] (CGM); B [3n] (MHD).  Synchronises. */
+ * rho [n]; u [3n] (with +F/2); phase [n] (CGM: the order parameter; Shan-Chen:
+ * the pseudopotential psi); B [3n] (MHD).  Synchronises. */
 lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *u, double *phase, double *B);
 
 /* FP64 reductions over all nodes of the current state: total mass sum rho,

@@ -21,7 +21,7 @@ from . import build as _build
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED = range(7)
 LBM_D3Q19 = 0
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
-PHYSICS = {"fluid": 0, "mhd": 1, "cgm": 2}
+PHYSICS = {"fluid": 0, "mhd": 1, "cgm": 2, "sc": 3}
 
 if not os.path.exists(_build.LIB):
     raise ImportError(f"liblbm.so is not built ({_build.LIB}); run paper_2010_01628_gb300.build.build() first")
@@ -45,7 +45,8 @@ class lbm_forcing(ctypes.Structure):
 
 class lbm_physparams(ctypes.Structure):
     _fields_ = [("tau_m", ctypes.c_double), ("b_wall", ctypes.c_double * 3), ("alpha_r", ctypes.c_double),
-                ("alpha_b", ctypes.c_double), ("A", ctypes.c_double), ("beta", ctypes.c_double)]
+                ("alpha_b", ctypes.c_double), ("A", ctypes.c_double), ("beta", ctypes.c_double),
+                ("G", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -154,8 +155,10 @@ def _ptr(a, n_expected=None, writable=False):
 
 def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0,
-               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
-    """Create a context; returns its handle (an int).  shape = (nx, ny, nz)."""
+               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
+    """Create a context; returns its handle (an int).  shape = (nx, ny, nz).
+    physics: "fluid", "mhd" (tau_m, b_wall), "cgm" (alpha_r, alpha_b, A, beta)
+    or "sc" (Shan-Chen, interaction strength G)."""
     if _alloc_refs is None and _torch() is not None:
         lbm_set_allocator(True)
     gr = lbm_grid()
@@ -172,6 +175,7 @@ def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.
     for a in range(3):
         ph.b_wall[a] = float(b_wall[a])
     ph.alpha_r, ph.alpha_b, ph.A, ph.beta = float(alpha_r), float(alpha_b), float(A), float(beta)
+    ph.G = float(G)
     ctx = _V()
     s = _current_stream() if stream is None else int(stream)
     _check(_lib.lbm_create(ctypes.byref(ctx), ctypes.byref(gr), LBM_D3Q19, ctypes.byref(rl), ctypes.byref(fo),

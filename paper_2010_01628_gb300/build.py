@@ -42,6 +42,7 @@ KERNEL_SOURCES = {
     "fluid": ["lbm_device.cuh", "lbm_fluid.cu"],
     "mhd": ["lbm_device.cuh", "lbm_mhd.cu"],
     "cgm": ["lbm_device.cuh", "lbm_cgm.cu"],
+    "sc": ["lbm_device.cuh", "lbm_fluid.cuh", "lbm_sc.cu"],
 }
 
 

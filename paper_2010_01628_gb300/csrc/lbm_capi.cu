@@ -71,6 +71,7 @@ cudaError_t phys_step(lbm_ctx* c, long n, bool dry = false) {
         case LBM_PHYS_FLUID: return lbm::fluid_step(c, n, dry);
         case LBM_PHYS_MHD: return lbm::mhd_step(c, n, dry);
         case LBM_PHYS_CGM: return lbm::cgm_step(c, n, dry);
+        case LBM_PHYS_SC: return lbm::sc_step(c, n, dry);
     }
     return cudaErrorInvalidValue;
 }
@@ -79,6 +80,7 @@ cudaError_t phys_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool unif
         case LBM_PHYS_FLUID: return lbm::fluid_init(c, slab, z0, nzs, uniform);
         case LBM_PHYS_MHD: return lbm::mhd_init(c, slab, z0, nzs, uniform);
         case LBM_PHYS_CGM: return lbm::cgm_init(c, slab, z0, nzs, uniform);
+        case LBM_PHYS_SC: return lbm::fluid_init(c, slab, z0, nzs, uniform);
     }
     return cudaErrorInvalidValue;
 }
@@ -87,6 +89,7 @@ cudaError_t phys_fields(lbm_ctx* c, double* slab, int z0, int nzs) {
         case LBM_PHYS_FLUID: return lbm::fluid_fields(c, slab, z0, nzs);
         case LBM_PHYS_MHD: return lbm::mhd_fields(c, slab, z0, nzs);
         case LBM_PHYS_CGM: return lbm::cgm_fields(c, slab, z0, nzs);
+        case LBM_PHYS_SC: return lbm::sc_fields(c, slab, z0, nzs);
     }
     return cudaErrorInvalidValue;
 }
@@ -95,6 +98,7 @@ cudaError_t phys_reduce(lbm_ctx* c, bool record) {
         case LBM_PHYS_FLUID: return lbm::fluid_reduce(c, record);
         case LBM_PHYS_MHD: return lbm::mhd_reduce(c, record);
         case LBM_PHYS_CGM: return lbm::cgm_reduce(c, record);
+        case LBM_PHYS_SC: return lbm::sc_reduce(c, record);
     }
     return cudaErrorInvalidValue;
 }
@@ -204,7 +208,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     if (cells >= 2147483648.0) return LBM_ERR_ARG;
     if (!(relax->omega > 0.0 && relax->omega < 2.0)) return LBM_ERR_ARG;
     if (relax->omega_bulk != 1.0 || relax->omega_3 != 1.0 || relax->omega_4 != 1.0) return LBM_ERR_UNSUPPORTED;
-    if ((int)physics < 0 || (int)physics > 2) return LBM_ERR_ARG;
+    if ((int)physics < 0 || (int)physics > 3) return LBM_ERR_ARG;
     if ((int)precision < 0 || (int)precision > 3) return LBM_ERR_ARG;
     if (physics != LBM_PHYS_FLUID && (precision == LBM_FP16_SHIFTED || precision == LBM_BF16_SHIFTED))
         return LBM_ERR_UNSUPPORTED;
@@ -217,6 +221,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
                          (grid->lid_u[0] != 0.0 || grid->lid_u[1] != 0.0 || grid->lid_u[2] != 0.0);
         if (lid) return LBM_ERR_UNSUPPORTED;
     }
+    if (physics == LBM_PHYS_SC && !std::isfinite(phys->G)) return LBM_ERR_ARG;
     if (physics == LBM_PHYS_MHD) {
         const bool lid = (grid->periodic_mask & 2u) == 0 &&
                          (grid->lid_u[0] != 0.0 || grid->lid_u[1] != 0.0 || grid->lid_u[2] != 0.0);
@@ -245,7 +250,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->box.periodic = grid->periodic_mask & 7u;
     c->box.n = (size_t)grid->nx * grid->ny * grid->nz;
     c->elem = precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
-    c->planes = physics == LBM_PHYS_FLUID ? 19 : (physics == LBM_PHYS_MHD ? 40 : 38);
+    c->planes = (physics == LBM_PHYS_FLUID || physics == LBM_PHYS_SC) ? 19 : (physics == LBM_PHYS_MHD ? 40 : 38);
     c->alloc = g_alloc;
     c->release = g_release;
     c->user = g_user;
@@ -265,10 +270,11 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->partials = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH * lbm::RED_BLOCKS);
     c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
     c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
-    if (physics == LBM_PHYS_CGM) c->phi = dev_alloc(c, c->box.n * cb);
+    const bool has_phi = physics == LBM_PHYS_CGM || physics == LBM_PHYS_SC;
+    if (has_phi) c->phi = dev_alloc(c, c->box.n * cb);
     c->status = (int*)dev_alloc(c, 256);
     bool ok = c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging && c->status &&
-              (physics != LBM_PHYS_CGM || c->phi);
+              (!has_phi || c->phi);
     if (ok && cudaMallocHost((void**)&c->result_host, sizeof(double) * lbm::RED_WIDTH) != cudaSuccess) {
         cudaGetLastError();
         c->result_host = nullptr;
@@ -380,7 +386,7 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* phase, double*
         if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho + off, s, m * 8, cudaMemcpyDefault, c->stream);
         for (int a = 0; a < 3 && e == cudaSuccess && u; ++a)
             e = cudaMemcpyAsync(u + a * n + off, s + (1 + a) * m, m * 8, cudaMemcpyDefault, c->stream);
-        if (e == cudaSuccess && phase && c->physics == LBM_PHYS_CGM)
+        if (e == cudaSuccess && phase && (c->physics == LBM_PHYS_CGM || c->physics == LBM_PHYS_SC))
             e = cudaMemcpyAsync(phase + off, s + 4 * m, m * 8, cudaMemcpyDefault, c->stream);
         for (int a = 0; a < 3 && e == cudaSuccess && B && c->physics == LBM_PHYS_MHD; ++a)
             e = cudaMemcpyAsync(B + a * n + off, s + (5 + a) * m, m * 8, cudaMemcpyDefault, c->stream);

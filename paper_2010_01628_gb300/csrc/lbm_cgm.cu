@@ -108,37 +108,14 @@ __global__ void __launch_bounds__(256) cgm_phi_kernel(const S* __restrict__ src,
     phi[self] = (sr - sb) / (sr + sb);
 }
 
-template <typename C, int I>
-__device__ __forceinline__ C phi_nbr(const C* __restrict__ phi, const Box& b, const Nbr& q, int x, int y, int z,
-                                     C own) {
-    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
-    const int sx = cx == 0 ? x : (cx > 0 ? q.xp : q.xm);
-    const int sy = cy == 0 ? y : (cy > 0 ? q.yp : q.ym);
-    const int sz = cz == 0 ? z : (cz > 0 ? q.zp : q.zm);
-    const bool wall = (cx > 0 && q.wxp) || (cx < 0 && q.wxm) || (cy > 0 && q.wyp) || (cy < 0 && q.wym) ||
-                      (cz > 0 && q.wzp) || (cz < 0 && q.wzm);
-    if (wall) return own;
-    return __ldg(phi + ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx);
-}
-
 template <typename C>
 __device__ __forceinline__ void grad_phi(const C* __restrict__ phi, const Box& b, const Nbr& q, int x, int y, int z,
                                          uint32_t self, C (&gr)[3]) {
-    const C own = phi[self];
-    C gx = (C)0, gy = (C)0, gz = (C)0;
-#define LBM_GP(I)                                                            \
-    {                                                                        \
-        const C v = phi_nbr<C, I>(phi, b, q, x, y, z, own) * (C)w_of(I);     \
-        if (cx_of(I)) gx += (C)cx_of(I) * v;                                 \
-        if (cy_of(I)) gy += (C)cy_of(I) * v;                                 \
-        if (cz_of(I)) gz += (C)cz_of(I) * v;                                 \
-    }
-    LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9) LBM_GP(10)
-    LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
-#undef LBM_GP
-    gr[0] = (C)3 * gx;
-    gr[1] = (C)3 * gy;
-    gr[2] = (C)3 * gz;
+    C s[3];
+    lattice_first_moment<C>(phi, b, q, x, y, z, phi[self], s);
+    gr[0] = (C)3 * s[0];
+    gr[1] = (C)3 * s[1];
+    gr[2] = (C)3 * s[2];
 }
 
 template <typename S, typename C, int I>

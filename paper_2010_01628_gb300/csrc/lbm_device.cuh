@@ -163,6 +163,43 @@ __device__ __forceinline__ void gather19(const S* __restrict__ src, const Box& b
 #undef LBM_G
 }
 
+// Value of a node field v at x + c_I; a neighbour behind a wall contributes
+// the node's own value `own`.
+template <typename C, int I>
+__device__ __forceinline__ C field_nbr(const C* __restrict__ v, const Box& b, const Nbr& q, int x, int y, int z,
+                                       C own) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    const int sx = cx == 0 ? x : (cx > 0 ? q.xp : q.xm);
+    const int sy = cy == 0 ? y : (cy > 0 ? q.yp : q.ym);
+    const int sz = cz == 0 ? z : (cz > 0 ? q.zp : q.zm);
+    const bool wall = (cx > 0 && q.wxp) || (cx < 0 && q.wxm) || (cy > 0 && q.wyp) || (cy < 0 && q.wym) ||
+                      (cz > 0 && q.wzp) || (cz < 0 && q.wzm);
+    if (wall) return own;
+    return __ldg(v + ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx);
+}
+
+// s = sum_i w_i c_i v(x + c_i) over the 18 moving directions: the lattice
+// first moment of a node field (times 1/c_s^2 the isotropic gradient of the
+// colour-gradient model; times -G psi(x) the Shan-Chen force).
+template <typename C>
+__device__ __forceinline__ void lattice_first_moment(const C* __restrict__ v, const Box& b, const Nbr& q, int x,
+                                                     int y, int z, C own, C (&s)[3]) {
+    C gx = (C)0, gy = (C)0, gz = (C)0;
+#define LBM_FM(I)                                                           \
+    {                                                                       \
+        const C t = field_nbr<C, I>(v, b, q, x, y, z, own) * (C)w_of(I);    \
+        if (cx_of(I)) gx += (C)cx_of(I) * t;                                \
+        if (cy_of(I)) gy += (C)cy_of(I) * t;                                \
+        if (cz_of(I)) gz += (C)cz_of(I) * t;                                \
+    }
+    LBM_FM(1) LBM_FM(2) LBM_FM(3) LBM_FM(4) LBM_FM(5) LBM_FM(6) LBM_FM(7) LBM_FM(8) LBM_FM(9) LBM_FM(10)
+    LBM_FM(11) LBM_FM(12) LBM_FM(13) LBM_FM(14) LBM_FM(15) LBM_FM(16) LBM_FM(17) LBM_FM(18)
+#undef LBM_FM
+    s[0] = gx;
+    s[1] = gy;
+    s[2] = gz;
+}
+
 template <typename S, typename C>
 __device__ __forceinline__ void scatter19(S* __restrict__ dst, size_t n, uint32_t self, const C (&f)[Q]) {
 #define LBM_STORE(I) store_shifted<S, C, I>(dst + (size_t)I * n + self, f[I]);
@@ -180,6 +217,7 @@ template <typename C>
 struct Moments {
     C drho, jx, jy, jz;
     C pxx_m_pyy, pyy_m_pzz, pxy, pxz, pyz;
+    C moving;  // sum of the 18 moving populations; drho = moving + f_0
 };
 
 template <typename C>
@@ -196,14 +234,28 @@ __device__ __forceinline__ Moments<C> moments19(const C (&f)[Q]) {
     m.jz = sz_p - sz_m;
     // sum_i f c_a^2: directions with c_a != 0 are exactly those counted above
     const C pxx = sx_p + sx_m, pyy = sy_p + sy_m, pzz = sz_p + sz_m;
-    // c_x = 0 directions: 0, 2, 3, 8, 9, 11, 12, 17, 18
-    m.drho = pxx + f[0] + (f[2] + f[11]) + (f[3] + f[12]) + (f[8] + f[17]) + (f[9] + f[18]);
+    // c_x = 0 directions: 0, 2, 3, 8, 9, 11, 12, 17, 18; the rest population
+    // is added last (conserve_mass relies on this order)
+    m.moving = pxx + (f[2] + f[11]) + (f[3] + f[12]) + (f[8] + f[17]) + (f[9] + f[18]);
+    m.drho = m.moving + f[0];
     m.pxx_m_pyy = pxx - pyy;
     m.pyy_m_pzz = pyy - pzz;
     m.pxy = (f[4] + f[13]) - (f[5] + f[14]);
     m.pxz = (f[6] + f[15]) - (f[7] + f[16]);
     m.pyz = (f[8] + f[17]) - (f[9] + f[18]);
     return m;
+}
+
+// Sets the rest population so that the 19 values sum to drho in the order of
+// the next step's density sum (moving directions first, f_0 last).  When drho
+// and the moving sum S are within a factor 2 of each other (a region whose
+// density is far from the reference, e.g. both phases of a multiphase run),
+// drho - S is exact (Sterbenz) and S + (drho - S) == drho, so a uniform region
+// keeps its mass exactly in FP32 instead of repeating the same rounding error
+// at every node and step.  Values are the shifted f - w.
+template <typename C>
+__device__ __forceinline__ void conserve_mass(C (&f)[Q], C drho) {
+    f[0] = drho - moments19(f).moving;
 }
 
 // ---------------------------------------------------------------------------

@@ -283,6 +283,7 @@ __global__ void fluid_init_kernel(S* __restrict__ dst, const double* __restrict_
     }
     C f[Q];
     equilibrium_shifted<C>(rho, drho, ux, uy, uz, f);
+    conserve_mass<C>(f, drho);
     scatter19<S, C>(dst, b.n, self, f);
 }
 

@@ -21,10 +21,10 @@ struct lbm_ctx {
     int device;
     lbm::Box box;
     size_t elem;      // bytes per stored population value
-    int planes;       // stored planes per state copy (19 fluid, 40 MHD, 38 CGM)
+    int planes;       // stored planes per state copy (19 fluid and Shan-Chen, 40 MHD, 38 CGM)
     void* buf[2];     // state copies (pull A-B); buf[cur] is current
     int cur;
-    void* phi;        // CGM order parameter (compute type)
+    void* phi;        // CGM order parameter / Shan-Chen pseudopotential (compute type)
     void* uprev;      // velocity recorded by the last reduction (compute type, 3 planes)
     bool have_prev;
     double* partials; // per-block reduction partials
@@ -88,6 +88,11 @@ cudaError_t cgm_step(lbm_ctx* c, long n, bool dry = false);
 cudaError_t cgm_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t cgm_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t cgm_reduce(lbm_ctx* c, bool record);
+
+// Shan-Chen (lbm_sc.cu); initialisation is the single-phase one.
+cudaError_t sc_step(lbm_ctx* c, long n, bool dry = false);
+cudaError_t sc_fields(lbm_ctx* c, double* slab, int z0, int nzs);
+cudaError_t sc_reduce(lbm_ctx* c, bool record);
 
 // Sum RED_BLOCKS partials into c->result (deterministic order).
 cudaError_t reduce_finalize(lbm_ctx* c);

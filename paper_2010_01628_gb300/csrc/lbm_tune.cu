@@ -108,7 +108,9 @@ bool save_cache(const char* path, const Cache& c) {
     return std::rename(tmp.c_str(), path) == 0;
 }
 
-const char* phys_name(lbm_physics p) { return p == LBM_PHYS_FLUID ? "fluid" : (p == LBM_PHYS_MHD ? "mhd" : "cgm"); }
+const char* phys_name(lbm_physics p) {
+    return p == LBM_PHYS_FLUID ? "fluid" : (p == LBM_PHYS_MHD ? "mhd" : (p == LBM_PHYS_CGM ? "cgm" : "sc"));
+}
 const char* prec_name(lbm_precision p) {
     return p == LBM_FP64 ? "fp64" : (p == LBM_FP32 ? "fp32" : (p == LBM_FP16_SHIFTED ? "fp16" : "bf16"));
 }

@@ -126,6 +126,31 @@ def droplets(n, seed=3, r_min=8.0, r_max=24.0, fraction=0.10, width=4.0, gap=4.0
     return rho, u, phase, spheres, vol / total
 
 
+def static_bubble(shape, radius, rho_l=1.95, rho_v=0.15, width=0.0, centre=None, axes=(0, 1, 2), noise=0.0,
+                  seed=0):
+    """Liquid droplet of density rho_l and radius ``radius`` in vapour rho_v,
+    at rest (the static-bubble workload: 100^3, R in [15, 30], 1.95 / 0.15).
+    width = 0 is the sharp step; width > 0 a tanh profile of that width.
+    ``axes`` lists the axes the distance is taken over (two axes: a cylinder
+    along the third).  ``noise`` adds i.i.d. U(-noise, noise) to u."""
+    nx, ny, nz = shape
+    x, y, z = grid(nx, ny, nz)
+    c = [(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0] if centre is None else list(centre)
+    d2 = np.zeros_like(x)
+    for a, v in zip((0, 1, 2), (x, y, z)):
+        if a in axes:
+            d2 += (v - c[a]) ** 2
+    d = np.sqrt(d2)
+    if width > 0:
+        rho = rho_v + (rho_l - rho_v) * 0.5 * (1.0 + np.tanh((radius - d) / width))
+    else:
+        rho = np.where(d <= radius, rho_l, rho_v)
+    u = np.zeros((3, nz, ny, nx))
+    if noise > 0:
+        u += np.random.default_rng(seed).uniform(-noise, noise, size=u.shape)
+    return rho, u
+
+
 def cavity_rest(n):
     return np.ones((n, n, n)), np.zeros((3, n, n, n))
 

@@ -17,7 +17,7 @@ def rel_l2(a, b):
 def oracle_run(shape, omega, steps, rho, u, phase=None, B=None, closed_form=True, threads=None, **kw):
     if threads:
         O.set_threads(threads)
-    phys = {"fluid": O.FLUID, "mhd": O.MHD, "cgm": O.CGM}[kw.pop("physics", "fluid")]
+    phys = {"fluid": O.FLUID, "mhd": O.MHD, "cgm": O.CGM, "sc": O.SC}[kw.pop("physics", "fluid")]
     d = O.Domain(shape, omega, physics=phys, closed_form=closed_form, **kw)
     d.init(rho, u, phase=phase, B=B)
     if steps:
@@ -39,7 +39,7 @@ def gpu_run(shape, omega, steps, rho, u, phase=None, B=None, precision="fp64", p
                           None if B is None else np.ascontiguousarray(B))
         if steps:
             L.lbm_step(ctx, steps)
-        want = ["rho", "u"] + (["phase"] if physics == "cgm" else []) + (["B"] if physics == "mhd" else [])
+        want = ["rho", "u"] + (["phase"] if physics in ("cgm", "sc") else []) + (["B"] if physics == "mhd" else [])
         out = L.lbm_fields(ctx, shape, want=want)
         if keep:
             out["ctx"] = ctx
