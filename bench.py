@@ -227,6 +227,8 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
         out.update(_cgm(L, timed, steps, peak, n_cgm))
     if only in (None, "sc"):
         out.update(_sc(L, timed, steps, peak))
+    if only in (None, "rt"):
+        out.update(_rt(L, timed, steps, peak))
     return out
 
 
@@ -323,6 +325,30 @@ def _sc(L, timed, steps, peak):
             "note": "two passes per step (pseudopotential, then collide with the interaction force); 160 B/LUP "
                     "algorithmic (19 populations read and written, psi written and read once)"}
     return out
+
+
+def _rt(L, timed, steps, peak):
+    # Rayleigh-Taylor (Sec. III.H) on the colour-gradient step: 64 x 256 x 64, rho 3 over 1, Re 512, At 0.5,
+    # walls at bottom and top, F = (rho - 2) g, FP32.  Timed from t = 0 (the interface is still flat-ish).
+    W = 64
+    g = 0.04 ** 2 / W
+    nu = W * 0.04 / 512.0
+    rho, u, phase = inputs.rayleigh_taylor(W)
+    shape = (W, 4 * W, W)
+    c = L.lbm_create(shape, 1 / (3 * nu + 0.5), periodic=(True, False, True), g=(0.0, -g, 0.0), rho_ref=2.0,
+                     physics="cgm", precision="fp32", alpha_r=7 / 9, alpha_b=1 / 3, A=0.0, beta=0.7)
+    L.lbm_init_fields(c, rho, u, phase=phase)
+    L.lbm_step(c, 3)
+    n_c = max(20, steps // 2) * 4
+    t = timed(lambda k: L.lbm_step(c, k), n_c)
+    L.lbm_reduce(c)
+    L.lbm_destroy(c)
+    cells = W * 4 * W * W
+    ach = 312 * cells * n_c / t / 1e9
+    return {"cgm_rayleigh_taylor_64x256x64": {
+        "MLUPS": cells * n_c / t / 1e6, "steps": n_c, "bytes_per_lup": 312, "moved_bytes_per_lup": 464,
+        "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
+        "note": "colour-gradient two-pass step with walls; 312 B/LUP algorithmic"}}
 
 
 def apply_launch(L, ctx, spec, tune_cache):
@@ -506,7 +532,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "sc", "fma-probe"], default=None,
+    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "sc", "rt", "fma-probe"], default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     ap.add_argument("--launch", default="auto",

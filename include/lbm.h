@@ -85,9 +85,14 @@ typedef struct {
     double omega, omega_bulk, omega_3, omega_4;
 } lbm_relax;
 
-/* Constant body acceleration: F = rho g (Sec. III.H, Eq. eq:posColl0). */
+/* Body force F = (rho - rho_ref) g (Eq. eq:posColl0): a constant acceleration
+ * for rho_ref = 0; the Rayleigh-Taylor test of Sec. III.H drives its two fluids
+ * with rho_ref = (rho_h + rho_l)/2.  rho_ref != 0 is accepted by the two-phase
+ * modules (LBM_PHYS_CGM, LBM_PHYS_SC); the other modules and the batch return
+ * LBM_ERR_UNSUPPORTED for it. */
 typedef struct {
     double g[3];
+    double rho_ref;
 } lbm_forcing;
 
 /* Physics-module parameters.
@@ -171,8 +176,8 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes);
  * kernel that performs all n steps with a bounded-wait grid barrier between
  * steps, replayed from a CUDA graph captured on first use (per step count and
  * buffer parity).  Physics: LBM_PHYS_FLUID or LBM_PHYS_MHD; FP64 or FP32.
- * grids/relax/forcing/phys are arrays of ndomains entries (forcing may be NULL;
- * phys is required for MHD).  Domain d is initialised, read back, reduced and
+ * grids/relax/forcing/phys are arrays of ndomains entries (forcing may be NULL,
+ * rho_ref must be 0; phys is required for MHD).  Domain d is initialised, read back, reduced and
  * checkpointed through its view (lbm_batch_domain), which accepts
  * lbm_init_fields, lbm_fields, lbm_reduce and lbm_get/set_populations; the view
  * is owned by the batch (lbm_destroy on it does nothing, lbm_step on it is
@@ -266,7 +271,8 @@ lbm_status lbm_probe_fma_rate(double *fp64_fma_per_s, double *fp32_fma_per_s);
  * would stall, code running inside an allocator or memory-pressure callback).
  * populations: device pointer to one state in the storage format of
  *   lbm_get_populations for LBM_PHYS_FLUID with this precision (19 planes).
- * grid, forcing: as for lbm_create (forcing may be NULL = no force).
+ * grid, forcing: as for lbm_create (forcing may be NULL = no force;
+ *   rho_ref != 0 gives LBM_ERR_UNSUPPORTED).
  * out: device-accessible pointer to 5 doubles, written with the sums over all
  *   nodes of rho, rho u (x, y, z; with +F/2) and the number of nodes with a
  *   non-finite value or rho <= 0, the same quantities lbm_reduce reports.

@@ -235,7 +235,7 @@ class _Params(ctypes.Structure):
                 ("tau_m", ctypes.c_double), ("b_wall", ctypes.c_double * 3),
                 ("alpha_r", ctypes.c_double), ("alpha_b", ctypes.c_double),
                 ("A", ctypes.c_double), ("beta", ctypes.c_double), ("nthreads", ctypes.c_int),
-                ("G", ctypes.c_double)]
+                ("G", ctypes.c_double), ("rho_ref", ctypes.c_double)]
 
 
 class Domain:
@@ -248,7 +248,7 @@ class Domain:
 
     def __init__(self, shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                  physics=FLUID, closed_form=True, omega_b=1.0, omega_3=1.0, omega_4=1.0, tau_m=1.0,
-                 b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0):
+                 b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz
@@ -265,6 +265,7 @@ class Domain:
         p.tau_m = float(tau_m)
         p.alpha_r, p.alpha_b, p.A, p.beta = map(float, (alpha_r, alpha_b, A, beta))
         p.G = float(G)
+        p.rho_ref = float(rho_ref)
         self.p = p
         self.physics = physics
         n = self.n

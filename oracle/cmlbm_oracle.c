@@ -520,6 +520,7 @@ typedef struct {
     double alpha_r, alpha_b, A, beta; /* CGM */
     int nthreads;
     double G; /* Shan-Chen interaction strength (physics 3) */
+    double rho_ref; /* body force F = (rho - rho_ref) g (Sec. III.H uses the mean density) */
 } orc_params;
 
 static long cell_index(const orc_params *p, int x, int y, int z)
@@ -666,10 +667,11 @@ static void node_macro(const orc_params *p, const double *fin, const double *gin
     double rho = s->rho;
     s->b[0] = s->b[1] = s->b[2] = 0.0;
     s->j[0] = s->j[1] = s->j[2] = 0.0;
-    /* Body force F = rho g (Sec. III.H uses a constant acceleration). */
-    s->F[0] = rho * p->g[0];
-    s->F[1] = rho * p->g[1];
-    s->F[2] = rho * p->g[2];
+    /* Body force F = (rho - rho_ref) g: a constant acceleration for rho_ref = 0;
+     * the Rayleigh-Taylor test (Sec. III.H) takes rho_ref = (rho_h + rho_l)/2. */
+    s->F[0] = (rho - p->rho_ref) * p->g[0];
+    s->F[1] = (rho - p->rho_ref) * p->g[1];
+    s->F[2] = (rho - p->rho_ref) * p->g[2];
     if (p->physics == 1 && gin) {
         double us[3] = {jx / rho, jy / rho, jz / rho};
         orc_current(gin, us[0], us[1], us[2], p->tau_m, s->b, s->j);
@@ -703,7 +705,7 @@ static void node_macro_sc(const orc_params *p, const double *fin, const double *
     raw_moments(fin, &s->rho, &jx, &jy, &jz);
     sc_force(p, psi, x, y, z, Fsc);
     for (int a = 0; a < 3; a++) {
-        s->F[a] = s->rho * p->g[a] + Fsc[a];
+        s->F[a] = (s->rho - p->rho_ref) * p->g[a] + Fsc[a];
         s->b[a] = s->j[a] = 0.0;
     }
     s->u[0] = (jx + 0.5 * s->F[0]) / s->rho;

@@ -40,7 +40,7 @@ class lbm_relax(ctypes.Structure):
 
 
 class lbm_forcing(ctypes.Structure):
-    _fields_ = [("g", ctypes.c_double * 3)]
+    _fields_ = [("g", ctypes.c_double * 3), ("rho_ref", ctypes.c_double)]
 
 
 class lbm_physparams(ctypes.Structure):
@@ -155,10 +155,12 @@ def _ptr(a, n_expected=None, writable=False):
 
 def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0,
-               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
+               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0, omega_bulk=1.0, omega_3=1.0, omega_4=1.0,
+               stream=None):
     """Create a context; returns its handle (an int).  shape = (nx, ny, nz).
     physics: "fluid", "mhd" (tau_m, b_wall), "cgm" (alpha_r, alpha_b, A, beta)
-    or "sc" (Shan-Chen, interaction strength G)."""
+    or "sc" (Shan-Chen, interaction strength G).  The body force is
+    F = (rho - rho_ref) g (rho_ref != 0: two-phase modules only)."""
     if _alloc_refs is None and _torch() is not None:
         lbm_set_allocator(True)
     gr = lbm_grid()
@@ -170,6 +172,7 @@ def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.
     fo = lbm_forcing()
     for a in range(3):
         fo.g[a] = float(g[a])
+    fo.rho_ref = float(rho_ref)
     ph = lbm_physparams()
     ph.tau_m = float(tau_m)
     for a in range(3):

@@ -222,6 +222,8 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
         if (lid) return LBM_ERR_UNSUPPORTED;
     }
     if (physics == LBM_PHYS_SC && !std::isfinite(phys->G)) return LBM_ERR_ARG;
+    if (forcing && forcing->rho_ref != 0.0 && physics != LBM_PHYS_CGM && physics != LBM_PHYS_SC)
+        return LBM_ERR_UNSUPPORTED;
     if (physics == LBM_PHYS_MHD) {
         const bool lid = (grid->periodic_mask & 2u) == 0 &&
                          (grid->lid_u[0] != 0.0 || grid->lid_u[1] != 0.0 || grid->lid_u[2] != 0.0);

@@ -21,6 +21,7 @@ struct CgmArgs {
     Box box;
     double omega, alpha_r, alpha_b, A, beta;
     double g[3];
+    double rg[3];  // rho_ref g: F = rho g - rho_ref g
 };
 
 template <typename C>
@@ -28,24 +29,31 @@ struct CgmNode {
     C rho_r, rho_b, rho, ux, uy, uz, Fx, Fy, Fz, alpha;
 };
 
+// Colour density: the 18 moving populations in direction order, then the rest
+// population.  The store below writes f_0 = rho_c - (that same moving sum), so
+// a uniform region sums back to its colour density exactly in FP32.
+template <typename C>
+__device__ __forceinline__ C colour_sum(const C (&f)[Q]) {
+    C s = f[1];
+#pragma unroll
+    for (int i = 2; i < Q; ++i) s += f[i];
+    return s + f[0];
+}
+
 template <typename C>
 __device__ __forceinline__ CgmNode<C> cgm_macro(const C (&fr)[Q], const C (&fb)[Q], C (&f)[Q], Moments<C>& m,
                                                 const CgmArgs& p) {
     CgmNode<C> s;
-    C sr = (C)0, sb = (C)0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        sr += fr[i];
-        sb += fb[i];
-        f[i] = fr[i] + fb[i];
-    }
+    for (int i = 0; i < Q; ++i) f[i] = fr[i] + fb[i];
     m = moments19(f);
+    const C sr = colour_sum(fr), sb = colour_sum(fb);
     s.rho_r = sr;
     s.rho_b = sb;
     s.rho = sr + sb;
-    s.Fx = s.rho * (C)p.g[0];
-    s.Fy = s.rho * (C)p.g[1];
-    s.Fz = s.rho * (C)p.g[2];
+    s.Fx = s.rho * (C)p.g[0] - (C)p.rg[0];
+    s.Fy = s.rho * (C)p.g[1] - (C)p.rg[1];
+    s.Fz = s.rho * (C)p.g[2] - (C)p.rg[2];
     const C inv = recip(s.rho);
     s.ux = (m.jx + (C)0.5 * s.Fx) * inv;
     s.uy = (m.jy + (C)0.5 * s.Fy) * inv;
@@ -99,12 +107,7 @@ __global__ void __launch_bounds__(256) cgm_phi_kernel(const S* __restrict__ src,
     C fr[Q], fb[Q];
     gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
     gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
-    C sr = (C)0, sb = (C)0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        sr += fr[i];
-        sb += fb[i];
-    }
+    const C sr = colour_sum(fr), sb = colour_sum(fb);
     phi[self] = (sr - sb) / (sr + sb);
 }
 
@@ -118,10 +121,13 @@ __device__ __forceinline__ void grad_phi(const C* __restrict__ phi, const Box& b
     gr[2] = (C)3 * s[2];
 }
 
+// Direction I (1..18) of the perturbed, recoloured populations; stores them
+// and adds them to the running colour sums (the rest direction is stored last
+// from the colour mass balance).
 template <typename S, typename C, int I>
 __device__ __forceinline__ void perturb_recolour_store(S* __restrict__ dst, size_t n, uint32_t self, C fi,
                                                        const C (&gr)[3], C n2, C pert_amp, C inv_n2, C inv_nrm,
-                                                       C frac_r, C frac_b, C sep, C alpha) {
+                                                       C frac_r, C frac_b, C sep, C alpha, C& sum_r, C& sum_b) {
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
     constexpr int c2 = cx * cx + cy * cy + cz * cz;
     const C cg = (C)cx * gr[0] + (C)cy * gr[1] + (C)cz * gr[2];
@@ -132,8 +138,16 @@ __device__ __forceinline__ void perturb_recolour_store(S* __restrict__ dst, size
     C cos_t = (C)0;
     if (c2 > 0 && inv_nrm > (C)0) cos_t = cg * inv_nrm * (C)(c2 == 1 ? 1.0 : 0.70710678118654752440);
     const C e = sep * cos_t * cgm_phi_i<C, I>(alpha);
-    Store<S>::store(dst + (size_t)I * n + self, frac_r * fi + e);
-    Store<S>::store(dst + (size_t)(Q + I) * n + self, frac_b * fi - e);
+    const C vr = frac_r * fi + e, vb = frac_b * fi - e;
+    Store<S>::store(dst + (size_t)I * n + self, vr);
+    Store<S>::store(dst + (size_t)(Q + I) * n + self, vb);
+    if (I == 1) {
+        sum_r = vr;
+        sum_b = vb;
+    } else {
+        sum_r += vr;
+        sum_b += vb;
+    }
 }
 
 template <typename S, typename C, bool WALLS>
@@ -162,11 +176,17 @@ __global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ 
     const C frac_r = s.rho_r * inv_rho, frac_b = s.rho_b * inv_rho;
     // beta rho_r rho_b / rho^2 * g_eq(rho, 0) with g_eq = rho phi_i(alpha)
     const C sep = (C)p.beta * s.rho_r * s.rho_b * inv_rho;
-#define LBM_PR(I) \
-    perturb_recolour_store<S, C, I>(dst, b.n, self, f[I], gr, n2, pert_amp, inv_n2, inv_nrm, frac_r, frac_b, sep, s.alpha);
-    LBM_PR(0) LBM_PR(1) LBM_PR(2) LBM_PR(3) LBM_PR(4) LBM_PR(5) LBM_PR(6) LBM_PR(7) LBM_PR(8) LBM_PR(9)
+    C sum_r, sum_b;
+#define LBM_PR(I)                                                                                             \
+    perturb_recolour_store<S, C, I>(dst, b.n, self, f[I], gr, n2, pert_amp, inv_n2, inv_nrm, frac_r, frac_b, sep, \
+                                    s.alpha, sum_r, sum_b);
+    LBM_PR(1) LBM_PR(2) LBM_PR(3) LBM_PR(4) LBM_PR(5) LBM_PR(6) LBM_PR(7) LBM_PR(8) LBM_PR(9)
     LBM_PR(10) LBM_PR(11) LBM_PR(12) LBM_PR(13) LBM_PR(14) LBM_PR(15) LBM_PR(16) LBM_PR(17) LBM_PR(18)
 #undef LBM_PR
+    // Rest direction: colour mass balance (perturbation and recolouring conserve
+    // each colour, and cos(theta_0) = 0).
+    Store<S>::store(dst + self, s.rho_r - sum_r);
+    Store<S>::store(dst + (size_t)Q * b.n + self, s.rho_b - sum_b);
 }
 
 template <typename S, typename C>
@@ -207,11 +227,17 @@ __global__ void cgm_init_kernel(S* __restrict__ dst, const double* __restrict__ 
     C h[Q];
     cgm_collide<C>(h, mz, s, (C)0);  // omega = 0 keeps kd = k5..9 = 0 exactly
     const C fr = (C)(rr / rho), fbl = (C)(rb / rho);
+    C sum_r = (C)0, sum_b = (C)0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        Store<S>::store(dst + (size_t)i * b.n + self, fr * h[i]);
-        Store<S>::store(dst + (size_t)(Q + i) * b.n + self, fbl * h[i]);
+    for (int i = 1; i < Q; ++i) {
+        const C vr = fr * h[i], vb = fbl * h[i];
+        Store<S>::store(dst + (size_t)i * b.n + self, vr);
+        Store<S>::store(dst + (size_t)(Q + i) * b.n + self, vb);
+        sum_r += vr;
+        sum_b += vb;
     }
+    Store<S>::store(dst + self, s.rho_r - sum_r);
+    Store<S>::store(dst + (size_t)Q * b.n + self, s.rho_b - sum_b);
 }
 
 template <typename S, typename C, bool WALLS>
@@ -274,7 +300,10 @@ static CgmArgs cgm_args(const lbm_ctx* c) {
     p.alpha_b = c->phys.alpha_b;
     p.A = c->phys.A;
     p.beta = c->phys.beta;
-    for (int a = 0; a < 3; ++a) p.g[a] = c->forcing.g[a];
+    for (int a = 0; a < 3; ++a) {
+        p.g[a] = c->forcing.g[a];
+        p.rg[a] = c->forcing.rho_ref * c->forcing.g[a];
+    }
     return p;
 }
 

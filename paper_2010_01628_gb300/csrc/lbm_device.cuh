@@ -247,12 +247,12 @@ __device__ __forceinline__ Moments<C> moments19(const C (&f)[Q]) {
 }
 
 // Sets the rest population so that the 19 values sum to drho in the order of
-// the next step's density sum (moving directions first, f_0 last).  When drho
-// and the moving sum S are within a factor 2 of each other (a region whose
-// density is far from the reference, e.g. both phases of a multiphase run),
-// drho - S is exact (Sterbenz) and S + (drho - S) == drho, so a uniform region
-// keeps its mass exactly in FP32 instead of repeating the same rounding error
-// at every node and step.  Values are the shifted f - w.
+// the next step's density sum (moving directions first, f_0 last).  The
+// rounding error of f_0 = drho - S is at most half an ulp of f_0, so whenever
+// |f_0| <= |drho| the next sum S + f_0 rounds back to drho itself (barring an
+// exact tie).  A uniform region (both phases of a multiphase run) then keeps
+// its mass exactly in FP32 instead of repeating the same rounding error at
+// every node and step.  Values are the shifted f - w.
 template <typename C>
 __device__ __forceinline__ void conserve_mass(C (&f)[Q], C drho) {
     f[0] = drho - moments19(f).moving;

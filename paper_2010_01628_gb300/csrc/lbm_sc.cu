@@ -27,6 +27,7 @@ struct ScArgs {
     Box box;
     double omega, G;
     double g[3];
+    double rg[3];  // rho_ref g: F = rho g - rho_ref g + F_sc
     double lid[3];
 };
 
@@ -45,9 +46,9 @@ __device__ __forceinline__ Macro<C> sc_macro(const Moments<C>& m, const C* __res
     C s[3];
     lattice_first_moment<C>(psi, b, q, x, y, z, own, s);
     const C mg = -(C)p.G * own;
-    a.Fx = a.rho * (C)p.g[0] + mg * s[0];
-    a.Fy = a.rho * (C)p.g[1] + mg * s[1];
-    a.Fz = a.rho * (C)p.g[2] + mg * s[2];
+    a.Fx = (a.rho * (C)p.g[0] - (C)p.rg[0]) + mg * s[0];
+    a.Fy = (a.rho * (C)p.g[1] - (C)p.rg[1]) + mg * s[1];
+    a.Fz = (a.rho * (C)p.g[2] - (C)p.rg[2]) + mg * s[2];
     const C inv = recip(a.rho);
     a.ux = (m.jx + (C)0.5 * a.Fx) * inv;
     a.uy = (m.jy + (C)0.5 * a.Fy) * inv;
@@ -145,6 +146,7 @@ static ScArgs sc_args(const lbm_ctx* c) {
     p.G = c->phys.G;
     for (int a = 0; a < 3; ++a) {
         p.g[a] = c->forcing.g[a];
+        p.rg[a] = c->forcing.rho_ref * c->forcing.g[a];
         p.lid[a] = (c->box.periodic & 2u) ? 0.0 : c->grid.lid_u[a];
     }
     return p;

@@ -151,6 +151,20 @@ def static_bubble(shape, radius, rho_l=1.95, rho_v=0.15, width=0.0, centre=None,
     return rho, u
 
 
+def rayleigh_taylor(W=64, rho_h=3.0, rho_l=1.0, amp=0.05, ny_factor=4):
+    """Rayleigh-Taylor start (Sec. III.H): a W x 4W x W box at rest, heavy
+    fluid (rho_h, order parameter +1) where y > 2W + amp W [cos(2 pi x/W) +
+    cos(2 pi z/W)], light fluid (rho_l, -1) below; node coordinates 0..n-1.
+    Returns (rho, u, phase) with the [nz][ny][nx] layout."""
+    nx, ny, nz = W, ny_factor * W, W
+    x, y, z = grid(nx, ny, nz)
+    surface = 0.5 * ny_factor * W + amp * W * (np.cos(2.0 * math.pi * x / W) + np.cos(2.0 * math.pi * z / W))
+    heavy = y > surface
+    rho = np.where(heavy, rho_h, rho_l)
+    phase = np.where(heavy, 1.0, -1.0)
+    return rho, np.zeros((3, nz, ny, nx)), phase
+
+
 def cavity_rest(n):
     return np.ones((n, n, n)), np.zeros((3, n, n, n))
 

@@ -531,3 +531,27 @@ def test_cgm_flat_interface_stays_put():
     zc0 = np.where(np.diff(np.sign(phase.ravel())))[0]
     zc1 = np.where(np.diff(np.sign(ph.ravel())))[0]
     np.testing.assert_array_equal(zc0, zc1)
+
+
+def test_reference_density_force_momentum_growth():
+    """F = (rho - rho_ref) g: on a periodic box the total momentum grows by
+    exactly (M - N rho_ref) g per step (Eq. eq:posColl0 adds F to rho u), for
+    the single-phase, colour-gradient and Shan-Chen steps alike."""
+    shape = (6, 5, 4)
+    n = 6 * 5 * 4
+    rng = np.random.default_rng(12)
+    rho = rng.uniform(0.8, 1.4, size=shape[::-1])
+    u = 0.01 * rng.standard_normal((3,) + shape[::-1])
+    g = np.array([2e-5, -3e-5, 1e-5])
+    for phys, extra in ((O.FLUID, {}), (O.CGM, {"alpha_r": 7 / 9, "alpha_b": 1 / 3, "A": 1e-4}),
+                        (O.SC, {"G": -1.0})):
+        d = O.Domain(shape, 1.3, physics=phys, g=tuple(g), rho_ref=1.1, **extra)
+        d.init(rho, u, phase=np.where(rho > 1.1, 1.0, -1.0) if phys == O.CGM else None)
+        r0, u0, _, _ = d.fields()
+        M = r0.sum()
+        p0 = (r0 * u0).sum(axis=(1, 2, 3))
+        d.step(7)
+        r1, u1, _, _ = d.fields()
+        p1 = (r1 * u1).sum(axis=(1, 2, 3))
+        assert abs(r1.sum() - M) < 1e-12 * M
+        np.testing.assert_allclose(p1 - p0, 7 * (M - n * 1.1) * g, rtol=1e-9, atol=1e-15)
