@@ -75,6 +75,7 @@ def _load():
             lib.orc_step.argtypes = [PP, P, P, P, P, P, P, P, P, P, ctypes.c_long]
             lib.orc_fields.argtypes = [PP, P, P, P, P, P, P, P, P]
             lib.orc_sc_force_field.argtypes = [PP, P, P]
+            lib.orc_regularize.argtypes = [P, I, P, P, D]
             _lib = lib
     return _lib
 
@@ -218,6 +219,15 @@ def cgm_recolour(f, grad, rho_r, rho_b, alpha, beta):
     return fr, fb
 
 
+def regularize(fin, sgn, u_w, g=(0.0, 0.0, 0.0), rho_ref=0.0):
+    """Regularized on-node wall reconstruction of one node (orc_regularize)."""
+    f = np.array(fin, dtype=np.float64)
+    uw = np.array(u_w, dtype=np.float64)
+    gg = np.array(g, dtype=np.float64)
+    _load().orc_regularize(_p(f), int(sgn), _p(uw), _p(gg), float(rho_ref))
+    return f
+
+
 def set_threads(n: int) -> None:
     _load().orc_set_threads(int(n))
 
@@ -235,7 +245,7 @@ class _Params(ctypes.Structure):
                 ("tau_m", ctypes.c_double), ("b_wall", ctypes.c_double * 3),
                 ("alpha_r", ctypes.c_double), ("alpha_b", ctypes.c_double),
                 ("A", ctypes.c_double), ("beta", ctypes.c_double), ("nthreads", ctypes.c_int),
-                ("G", ctypes.c_double), ("rho_ref", ctypes.c_double)]
+                ("G", ctypes.c_double), ("rho_ref", ctypes.c_double), ("wall_model", ctypes.c_int)]
 
 
 class Domain:
@@ -248,7 +258,8 @@ class Domain:
 
     def __init__(self, shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                  physics=FLUID, closed_form=True, omega_b=1.0, omega_3=1.0, omega_4=1.0, tau_m=1.0,
-                 b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0):
+                 b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0,
+                 wall_model="bounce_back"):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz
@@ -266,6 +277,13 @@ class Domain:
         p.alpha_r, p.alpha_b, p.A, p.beta = map(float, (alpha_r, alpha_b, A, beta))
         p.G = float(G)
         p.rho_ref = float(rho_ref)
+        if wall_model not in ("bounce_back", "regularized"):
+            raise ValueError(wall_model)
+        if wall_model == "regularized":
+            # on-node walls at y = 0 and y = ny - 1 only (straight channel walls)
+            if periodic[1] or not (periodic[0] and periodic[2]) or ny < 3 or physics != FLUID:
+                raise ValueError("regularized walls: single phase, walls on y only, ny >= 3")
+        p.wall_model = 1 if wall_model == "regularized" else 0
         self.p = p
         self.physics = physics
         n = self.n

@@ -521,6 +521,7 @@ typedef struct {
     int nthreads;
     double G; /* Shan-Chen interaction strength (physics 3) */
     double rho_ref; /* body force F = (rho - rho_ref) g (Sec. III.H uses the mean density) */
+    int wall_model; /* 0: half-way bounce-back; 1: regularized on-node walls on the y axis */
 } orc_params;
 
 static long cell_index(const orc_params *p, int x, int y, int z)
@@ -535,6 +536,51 @@ static int wrap(int v, int n, int periodic)
     if (v >= 0 && v < n) return v;
     if (!periodic) return -1;
     return ((v % n) + n) % n;
+}
+
+/* Regularized on-node wall (Sec. III opening paragraph cites Latt, Chopard,
+ * Malaspinas, Deville and Michler, Phys. Rev. E 77, 056703 (2008), "straight
+ * velocity boundaries"): the wall lies on the boundary node, whose velocity is
+ * the wall's.  fin holds the pulled populations; those with c_y = sgn (sgn the
+ * y component of the inward normal: +1 at y = 0, -1 at y = ny - 1) came from
+ * outside and are unknown.
+ *  1. rho from the known ones: the normal momentum of the bare populations is
+ *     rho u_n - F_n/2 (rho u = Sum f c + F/2, F = (rho - rho_ref) g), so
+ *     rho (1 - u_n + g_n/2) = rho_0 + 2 rho_out + rho_ref g_n/2, rho_0 the sum
+ *     over c_y = 0 and rho_out over c_y = -sgn;
+ *  2. f_eq = the extended equilibrium at rho and u_eq = u_w - F/(2 rho), so that
+ *     the corrected velocity equals u_w;
+ *  3. unknown populations: bounce-back of the non-equilibrium part,
+ *     f_i = f_eq_i + f_opp(i) - f_eq_opp(i);
+ *  4. Pi_neq = Sum_i c_i c_i (f_i - f_eq_i) over all 19;
+ *  5. every population is replaced by f_eq_i + w_i/(2 cs^4) Q_i : Pi_neq,
+ *     Q_i = c_i c_i - cs^2 I. */
+void orc_regularize(double *fin, int sgn, const double *u_w, const double *g, double rho_ref)
+{
+    double rho0 = 0, rout = 0;
+    for (int i = 0; i < Q; i++) {
+        if (CY[i] == 0) rho0 += fin[i];
+        if (CY[i] == -sgn) rout += fin[i];
+    }
+    double gn = sgn * g[1], un = sgn * u_w[1];
+    double rho = (rho0 + 2.0 * rout + 0.5 * rho_ref * gn) / (1.0 - un + 0.5 * gn);
+    double ueq[3], feq[Q], pi[3][3] = {{0}};
+    for (int a = 0; a < 3; a++) ueq[a] = u_w[a] - 0.5 * (rho - rho_ref) * g[a] / rho;
+    orc_feq(rho, ueq[0], ueq[1], ueq[2], feq);
+    for (int i = 0; i < Q; i++)
+        if (CY[i] == sgn) fin[i] = feq[i] + fin[opposite(i)] - feq[opposite(i)];
+    for (int i = 0; i < Q; i++) {
+        double c[3] = {CX[i], CY[i], CZ[i]}, d = fin[i] - feq[i];
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) pi[a][b] += c[a] * c[b] * d;
+    }
+    double tr = pi[0][0] + pi[1][1] + pi[2][2];
+    for (int i = 0; i < Q; i++) {
+        double c[3] = {CX[i], CY[i], CZ[i]}, qp = -CS2 * tr;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) qp += c[a] * c[b] * pi[a][b];
+        fin[i] = feq[i] + weight(i) / (2.0 * CS2 * CS2) * qp;
+    }
 }
 
 /* Streaming, Eq. (streaming), in gather form: f_i(x, t+1) = f*_i(x - c_i, t).
@@ -558,6 +604,11 @@ static void gather_f(const orc_params *p, const double *fpost, int x, int y, int
             }
             fin[i] = v;
         }
+    }
+    /* regularized walls replace the bounce-back values on the y boundary nodes */
+    if (lid_term && p->wall_model == 1 && !p->periodic[1] && (y == 0 || y == p->ny - 1)) {
+        const double rest[3] = {0.0, 0.0, 0.0};
+        orc_regularize(fin, y == 0 ? 1 : -1, y == 0 ? rest : p->lid_u, p->g, p->rho_ref);
     }
 }
 
