@@ -67,14 +67,25 @@ typedef enum {
     LBM_PHYS_SC = 3     /* Shan-Chen pseudopotential multiphase (Sec. III.G)      */
 } lbm_physics;
 
-/* Box geometry.  A periodic axis wraps; a non-periodic axis has half-way
- * bounce-back no-slip walls at both ends (the paper's regularized walls,
- * Sec. III, are not implemented).  lid_u is the velocity of the +y wall
- * (Ladd's moving-wall term with rho_w = 1); it is ignored if y is periodic. */
+/* Wall models.  LBM_WALL_BOUNCE_BACK: half-way bounce-back, the wall midway
+ * between the boundary node and the next (virtual) node.  LBM_WALL_REGULARIZED:
+ * the regularized on-node walls the paper imposes (Sec. III opening paragraph,
+ * citing Latt, Chopard, Malaspinas, Deville and Michler, Phys. Rev. E 77,
+ * 056703 (2008)): the wall lies on the boundary nodes y = 0 and y = ny - 1,
+ * whose populations are rebuilt from rho (from the known populations), the wall
+ * velocity and the non-equilibrium stress; straight channel walls only
+ * (LBM_PHYS_FLUID, walls on y, x and z periodic, ny >= 3). */
+typedef enum { LBM_WALL_BOUNCE_BACK = 0, LBM_WALL_REGULARIZED = 1 } lbm_wall_model;
+
+/* Box geometry.  A periodic axis wraps; a non-periodic axis has no-slip walls
+ * at both ends, of the given wall model.  lid_u is the velocity of the +y wall
+ * (bounce-back: Ladd's moving-wall term with rho_w = 1; regularized: the
+ * velocity of the y = ny - 1 nodes); it is ignored if y is periodic. */
 typedef struct {
     int nx, ny, nz;
     unsigned periodic_mask; /* bit 0: x, bit 1: y, bit 2: z */
     double lid_u[3];
+    int wall_model;         /* lbm_wall_model */
 } lbm_grid;
 
 /* Diagonal relaxation matrix K of Sec. II.B: omega on the five deviatoric

@@ -222,6 +222,10 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
         if (lid) return LBM_ERR_UNSUPPORTED;
     }
     if (physics == LBM_PHYS_SC && !std::isfinite(phys->G)) return LBM_ERR_ARG;
+    if (grid->wall_model != LBM_WALL_BOUNCE_BACK && grid->wall_model != LBM_WALL_REGULARIZED) return LBM_ERR_ARG;
+    if (grid->wall_model == LBM_WALL_REGULARIZED &&
+        (physics != LBM_PHYS_FLUID || (grid->periodic_mask & 7u) != 5u || grid->ny < 3))
+        return LBM_ERR_UNSUPPORTED;
     if (forcing && forcing->rho_ref != 0.0 && physics != LBM_PHYS_CGM && physics != LBM_PHYS_SC)
         return LBM_ERR_UNSUPPORTED;
     if (physics == LBM_PHYS_MHD) {

@@ -21,6 +21,25 @@ __global__ void __launch_bounds__(256) fluid_step_kernel(const S* __restrict__ s
     fluid_node<S, C, WALLS, true>(src, dst, p, x, blockIdx.y, blockIdx.z);
 }
 
+// Regularized on-node walls on y (x, z periodic).  One block row is one y, so
+// the wall rows branch as whole blocks.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) fluid_step_reg_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                             FluidArgs p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const Box& b = p.box;
+    if (x >= b.nx) return;
+    const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    const Nbr q = make_nbr(b, x, y, z);
+    C f[Q];
+    gather_regularized<S, C>(src, p, q, x, y, z, self, f);
+    const Moments<C> m = moments19(f);
+    const Macro<C> a = fluid_macro(m, (C)p.g[0], (C)p.g[1], (C)p.g[2]);
+    collide_fluid<C>(f, m, a, (C)p.omega);
+    scatter19<S, C>(dst, b.n, self, f);
+}
+
 // ---------------------------------------------------------------------------
 // 16-bit storage, two adjacent x-cells per thread.  A thread owns the 32-bit
 // word holding cells (x0, x0+1), x0 even, of every plane: all loads and stores
@@ -287,8 +306,9 @@ __global__ void fluid_init_kernel(S* __restrict__ dst, const double* __restrict_
     scatter19<S, C>(dst, b.n, self, f);
 }
 
-// Moments of the gathered state for a z-slab: rho, u (with +F/2).
-template <typename S, typename C, bool WALLS>
+// Moments of the gathered state for a z-slab: rho, u (with +F/2).  REG: the
+// regularized walls' rebuilt populations on the wall rows.
+template <typename S, typename C, bool WALLS, bool REG = false>
 __global__ void fluid_fields_kernel(const S* __restrict__ src, double* __restrict__ slab, FluidArgs p, int z0,
                                     int nzs) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,7 +321,10 @@ __global__ void fluid_fields_kernel(const S* __restrict__ src, double* __restric
     const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
     const Nbr q = make_nbr(b, x, y, z);
     C f[Q];
-    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)p.lid[0], (C)p.lid[1], (C)p.lid[2], f);
+    if (REG)
+        gather_regularized<S, C>(src, p, q, x, y, z, self, f);
+    else
+        gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)p.lid[0], (C)p.lid[1], (C)p.lid[2], f);
     const Moments<C> mo = moments19(f);
     const Macro<C> a = fluid_macro(mo, (C)p.g[0], (C)p.g[1], (C)p.g[2]);
     slab[k] = (double)a.rho;
@@ -310,7 +333,7 @@ __global__ void fluid_fields_kernel(const S* __restrict__ src, double* __restric
     slab[3 * m + k] = (double)a.uz;
 }
 
-template <typename S, typename C, bool WALLS>
+template <typename S, typename C, bool WALLS, bool REG = false>
 __global__ void __launch_bounds__(RED_THREADS) fluid_reduce_kernel(const S* __restrict__ src, FluidArgs p,
                                                                    C* __restrict__ uprev, bool have_prev,
                                                                    bool record, double* __restrict__ partials) {
@@ -328,7 +351,10 @@ __global__ void __launch_bounds__(RED_THREADS) fluid_reduce_kernel(const S* __re
             const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
             const Nbr q = make_nbr(b, x, y, z);
             C f[Q];
-            gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)p.lid[0], (C)p.lid[1], (C)p.lid[2], f);
+            if (REG)
+                gather_regularized<S, C>(src, p, q, x, y, z, self, f);
+            else
+                gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)p.lid[0], (C)p.lid[1], (C)p.lid[2], f);
             const Moments<C> mo = moments19(f);
             const Macro<C> a = fluid_macro(mo, (C)p.g[0], (C)p.g[1], (C)p.g[2]);
             reduce_node<C>(acc, a.rho, a.ux, a.uy, a.uz, uprev, b.n, self, have_prev, record);
@@ -367,7 +393,7 @@ static size_t tma_smem_bytes(const lbm_ctx* c, int stages) {
 }
 
 int fluid_tma_max_stages(const lbm_ctx* c, int ctas) {
-    if (c->physics != LBM_PHYS_FLUID || ctas < 1 || ctas > 4) return 0;
+    if (c->physics != LBM_PHYS_FLUID || c->grid.wall_model != LBM_WALL_BOUNCE_BACK || ctas < 1 || ctas > 4) return 0;
     if (((size_t)c->box.nx * c->elem) % 16 != 0 || c->box.nx < 32) return 0;
     const size_t budget = (ctas == 1 ? SMEM_PER_BLOCK_OPTIN : SMEM_PER_SM / (size_t)ctas - 1024) - 256;
     int st = 0;
@@ -405,6 +431,15 @@ static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const FluidArgs p = fluid_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
+    if (c->grid.wall_model == LBM_WALL_REGULARIZED) {
+        const dim3 grid = step_grid(c->box, bx);
+        for (long s = 0; s < n; ++s) {
+            fluid_step_reg_kernel<S, C><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], (S*)c->buf[c->cur ^ 1],
+                                                                    p);
+            if (!dry) c->cur ^= 1;
+        }
+        return cudaGetLastError();
+    }
     if (c->variant == 1 && c->tma_stages >= 2 && c->tma_stages <= fluid_tma_max_stages(c, c->tma_ctas)) {
         for (long s = 0; s < n; ++s) {
             const S* src = (const S*)c->buf[c->cur];
@@ -453,7 +488,9 @@ static cudaError_t fields_t(lbm_ctx* c, double* slab, int z0, int nzs) {
     const FluidArgs p = fluid_args(c);
     const int bx = c->block_x;
     dim3 grid((unsigned)((c->box.nx + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)nzs);
-    if ((c->box.periodic & 7u) != 7u)
+    if (c->grid.wall_model == LBM_WALL_REGULARIZED)
+        fluid_fields_kernel<S, C, true, true><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], slab, p, z0, nzs);
+    else if ((c->box.periodic & 7u) != 7u)
         fluid_fields_kernel<S, C, true><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], slab, p, z0, nzs);
     else
         fluid_fields_kernel<S, C, false><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], slab, p, z0, nzs);
@@ -463,7 +500,10 @@ static cudaError_t fields_t(lbm_ctx* c, double* slab, int z0, int nzs) {
 template <typename S, typename C>
 static cudaError_t reduce_t(lbm_ctx* c, bool record) {
     const FluidArgs p = fluid_args(c);
-    if ((c->box.periodic & 7u) != 7u)
+    if (c->grid.wall_model == LBM_WALL_REGULARIZED)
+        fluid_reduce_kernel<S, C, true, true><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
+            (const S*)c->buf[c->cur], p, (C*)c->uprev, c->have_prev, record, c->partials);
+    else if ((c->box.periodic & 7u) != 7u)
         fluid_reduce_kernel<S, C, true><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
             (const S*)c->buf[c->cur], p, (C*)c->uprev, c->have_prev, record, c->partials);
     else

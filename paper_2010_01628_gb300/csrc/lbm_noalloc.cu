@@ -147,6 +147,8 @@ extern "C" lbm_status lbm_reduce_state_noalloc(const void* populations, lbm_prec
         return set_err(err, err_len, LBM_ERR_ARG, "grid sizes must be >= 1");
     if (grid->ny > 65535 || grid->nz > 65535)
         return set_err(err, err_len, LBM_ERR_ARG, "ny and nz are limited to 65535");
+    if (grid->wall_model != LBM_WALL_BOUNCE_BACK)
+        return set_err(err, err_len, LBM_ERR_UNSUPPORTED, "only half-way bounce-back walls are supported here");
     if (forcing && forcing->rho_ref != 0.0)
         return set_err(err, err_len, LBM_ERR_UNSUPPORTED, "rho_ref != 0 is supported by the two-phase modules only");
     const double cells = (double)grid->nx * grid->ny * grid->nz;

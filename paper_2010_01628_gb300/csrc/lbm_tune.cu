@@ -121,8 +121,9 @@ std::string cache_key(const lbm_ctx* c, const std::vector<long>& domain_sizes) {
     if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) dev = prop.name;
     char buf[256];
     if (!c->batch) {
-        std::snprintf(buf, sizeof(buf), "%s|%s|%s|%dx%dx%d|p%u", dev.c_str(), phys_name(c->physics),
-                      prec_name(c->prec), c->box.nx, c->box.ny, c->box.nz, c->box.periodic);
+        std::snprintf(buf, sizeof(buf), "%s|%s|%s|%dx%dx%d|p%u%s", dev.c_str(), phys_name(c->physics),
+                      prec_name(c->prec), c->box.nx, c->box.ny, c->box.nz, c->box.periodic,
+                      c->grid.wall_model == LBM_WALL_REGULARIZED ? "|reg" : "");
         return buf;
     }
     unsigned long long h = 1469598103934665603ull;  // FNV-1a over the domain sizes
@@ -158,7 +159,8 @@ extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads,
     if (threads < 32 || threads > 256 || threads % 32 != 0) return LBM_ERR_ARG;
     if (variant == 0 || variant == 2) {
         if (variant == 2 && !(c->physics == LBM_PHYS_FLUID &&
-                              (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) && c->box.nx % 2 == 0))
+                              (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) && c->box.nx % 2 == 0 &&
+                              c->grid.wall_model == LBM_WALL_BOUNCE_BACK))
             return LBM_ERR_UNSUPPORTED;
         c->variant = variant;
         c->block_x = threads;
@@ -256,7 +258,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
         std::vector<Cand> cands;
         for (int bx : {64, 128, 256}) cands.push_back({0, bx, 0, 1});
         if (c->physics == LBM_PHYS_FLUID && (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) &&
-            c->box.nx % 2 == 0)
+            c->box.nx % 2 == 0 && c->grid.wall_model == LBM_WALL_BOUNCE_BACK)
             for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
         for (int ctas : {1, 2, 3, 4}) {
             const int smax = lbm::fluid_tma_max_stages(c, ctas);
