@@ -371,7 +371,8 @@ def _channel(L, timed, steps, peak):
     return {"fluid_regularized_channel_512": {
         "MLUPS": n ** 3 * n_c / t / 1e6, "steps": n_c, "bytes_per_lup": 152, "achieved_GBps": ach,
         "frac_of_hbm_peak": ach / peak,
-        "note": "fluid_step_reg_kernel: regularized walls rebuild the y = 0 and y = n - 1 rows"}}
+        "note": "fluid_step_interior_kernel (rows 1..n-2, periodic node code) + fluid_step_wallrows_kernel "
+                "(regularized rebuild of rows 0 and n-1)"}}
 
 
 def apply_launch(L, ctx, spec, tune_cache):

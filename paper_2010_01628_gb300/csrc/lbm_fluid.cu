@@ -21,15 +21,31 @@ __global__ void __launch_bounds__(256) fluid_step_kernel(const S* __restrict__ s
     fluid_node<S, C, WALLS, true>(src, dst, p, x, blockIdx.y, blockIdx.z);
 }
 
-// Regularized on-node walls on y (x, z periodic).  One block row is one y, so
-// the wall rows branch as whole blocks.
+// Channels (x and z periodic, walls on y, ny >= 3) step in two launches: the
+// interior rows 1 .. ny-2 never pull through a wall and run the periodic node
+// code (40 registers instead of 48); a small launch then updates the two wall
+// rows with bounce-back or regularized walls.
 template <typename S, typename C>
-__global__ void __launch_bounds__(256) fluid_step_reg_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                             FluidArgs p) {
+__global__ void __launch_bounds__(256) fluid_step_interior_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                                  FluidArgs p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.box.nx) return;
+    fluid_node<S, C, false, true>(src, dst, p, x, blockIdx.y + 1, blockIdx.z);
+}
+
+// The wall rows y = 0 (blockIdx.y = 0) and y = ny - 1 (blockIdx.y = 1) of a
+// channel.  REG: regularized on-node walls; else half-way bounce-back with the lid.
+template <typename S, typename C, bool REG>
+__global__ void __launch_bounds__(256) fluid_step_wallrows_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                                  FluidArgs p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const Box& b = p.box;
+    const int y = blockIdx.y == 0 ? 0 : b.ny - 1, z = blockIdx.z;
     if (x >= b.nx) return;
+    if (!REG) {
+        fluid_node<S, C, true, true>(src, dst, p, x, y, z);
+        return;
+    }
     const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
     const Nbr q = make_nbr(b, x, y, z);
     C f[Q];
@@ -431,11 +447,19 @@ static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const FluidArgs p = fluid_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
-    if (c->grid.wall_model == LBM_WALL_REGULARIZED) {
-        const dim3 grid = step_grid(c->box, bx);
+    const bool reg = c->grid.wall_model == LBM_WALL_REGULARIZED;
+    const bool channel = (c->box.periodic & 7u) == 5u && c->box.ny >= 3;
+    if (channel && (reg || c->variant == 0)) {
+        const unsigned gx = (unsigned)((c->box.nx + bx - 1) / bx);
+        const dim3 inner(gx, (unsigned)(c->box.ny - 2), (unsigned)c->box.nz), rows(gx, 2u, (unsigned)c->box.nz);
         for (long s = 0; s < n; ++s) {
-            fluid_step_reg_kernel<S, C><<<grid, bx, 0, c->stream>>>((const S*)c->buf[c->cur], (S*)c->buf[c->cur ^ 1],
-                                                                    p);
+            const S* src = (const S*)c->buf[c->cur];
+            S* dst = (S*)c->buf[c->cur ^ 1];
+            fluid_step_interior_kernel<S, C><<<inner, bx, 0, c->stream>>>(src, dst, p);
+            if (reg)
+                fluid_step_wallrows_kernel<S, C, true><<<rows, bx, 0, c->stream>>>(src, dst, p);
+            else
+                fluid_step_wallrows_kernel<S, C, false><<<rows, bx, 0, c->stream>>>(src, dst, p);
             if (!dry) c->cur ^= 1;
         }
         return cudaGetLastError();

@@ -128,3 +128,16 @@ def test_reductions_match_oracle_fp64():
         L.lbm_destroy(ctx)
     assert math.isclose(m, o["rho"].sum(), rel_tol=1e-13)
     np.testing.assert_allclose(p, (o["rho"] * o["u"]).sum(axis=(1, 2, 3)), rtol=0, atol=1e-12 * m)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("wall_model", ["bounce_back", "regularized"])
+def test_channel_split_launch_parity(precision, wall_model):
+    """Channels step as an interior launch plus a wall-row launch; half-way
+    bounce-back and regularized walls, lid and body force, ragged x."""
+    shape = (45, 7, 3)
+    rho, u = inputs.random_fields(shape, seed=64, u_amp=0.03)
+    kw = dict(periodic=(True, False, True), wall_model=wall_model, lid_u=(0.04, 0.0, 0.01), g=(1e-5, -2e-6, 0.0))
+    o = oracle_run(shape, 1.3, 20, rho, u, **kw)
+    r = gpu_run(shape, 1.3, 20, rho, u, precision=precision, **kw)
+    compare(r, o, TOL[precision])
