@@ -76,6 +76,9 @@ def _load():
             lib.orc_fields.argtypes = [PP, P, P, P, P, P, P, P, P]
             lib.orc_sc_force_field.argtypes = [PP, P, P]
             lib.orc_regularize.argtypes = [P, I, P, P, D]
+            lib.orc_collide_rm.argtypes = [P, D, D, D, D, D, D, D, D, P]
+            lib.orc_collide_rm.restype = None
+            lib.orc_collide_dense_rm.argtypes = [P, D, D, D, D, D, D, D, D, P]
             _lib = lib
     return _lib
 
@@ -219,6 +222,16 @@ def cgm_recolour(f, grad, rho_r, rho_b, alpha, beta):
     return fr, fb
 
 
+def collide_rm(f, rho, u, F, omega, dense=False):
+    """Raw-moment variant of App. C: the printed list (closed) or the MRT
+    definition with M = T(0) (dense)."""
+    out = _vec()
+    fn = _load().orc_collide_dense_rm if dense else _load().orc_collide_rm
+    fn(_p(np.ascontiguousarray(f, dtype=np.float64)), float(rho), *map(float, u), *map(float, F), float(omega),
+       _p(out))
+    return out
+
+
 def regularize(fin, sgn, u_w, g=(0.0, 0.0, 0.0), rho_ref=0.0):
     """Regularized on-node wall reconstruction of one node (orc_regularize)."""
     f = np.array(fin, dtype=np.float64)
@@ -245,7 +258,8 @@ class _Params(ctypes.Structure):
                 ("tau_m", ctypes.c_double), ("b_wall", ctypes.c_double * 3),
                 ("alpha_r", ctypes.c_double), ("alpha_b", ctypes.c_double),
                 ("A", ctypes.c_double), ("beta", ctypes.c_double), ("nthreads", ctypes.c_int),
-                ("G", ctypes.c_double), ("rho_ref", ctypes.c_double), ("wall_model", ctypes.c_int)]
+                ("G", ctypes.c_double), ("rho_ref", ctypes.c_double), ("wall_model", ctypes.c_int),
+                ("raw_moments", ctypes.c_int)]
 
 
 class Domain:
@@ -259,7 +273,7 @@ class Domain:
     def __init__(self, shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                  physics=FLUID, closed_form=True, omega_b=1.0, omega_3=1.0, omega_4=1.0, tau_m=1.0,
                  b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0, alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0,
-                 wall_model="bounce_back"):
+                 wall_model="bounce_back", collision="cm"):
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz
@@ -284,6 +298,9 @@ class Domain:
             if periodic[1] or not (periodic[0] and periodic[2]) or ny < 3 or physics != FLUID:
                 raise ValueError("regularized walls: single phase, walls on y only, ny >= 3")
         p.wall_model = 1 if wall_model == "regularized" else 0
+        if collision not in ("cm", "rm"):
+            raise ValueError(collision)
+        p.raw_moments = int(collision == "rm")
         self.p = p
         self.physics = physics
         n = self.n

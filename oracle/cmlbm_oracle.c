@@ -370,6 +370,30 @@ void orc_kstar_cgm(const double *f, double rho, double ux, double uy, double uz,
     ks[18] = rho * (1.0 + uy * uy + uz * uz - alpha * (1.0 + 3.0 * uy * uy + 3.0 * uz * uz)) / 6.0;
 }
 
+/* App. C, Eq. (pdfQ19): populations from raw moments, f = M^-1 r. */
+static void raw_to_populations(const double *r, double *f)
+{
+    f[0] = r[0] - r[4] + r[16] + r[17] + r[18];
+    f[1] = (r[11] + r[13] - r[1] - r[16] - r[17]) / 2.0 + (r[4] + 2.0 * r[5] + r[6]) * CS2 / 2.0;
+    f[2] = (r[10] + r[15] - r[2] - r[16] - r[18]) / 2.0 + (r[4] + r[6] - r[5]) * CS2 / 2.0;
+    f[3] = (r[12] + r[14] - r[3] - r[17] - r[18]) / 2.0 + (r[4] - r[5] - 2.0 * r[6]) * CS2 / 2.0;
+    f[4] = (r[7] + r[16] - r[10] - r[11]) / 4.0;
+    f[5] = (r[10] + r[16] - r[7] - r[11]) / 4.0;
+    f[6] = (r[8] + r[17] - r[12] - r[13]) / 4.0;
+    f[7] = (r[12] + r[17] - r[8] - r[13]) / 4.0;
+    f[8] = (r[9] + r[18] - r[14] - r[15]) / 4.0;
+    f[9] = (r[14] + r[18] - r[9] - r[15]) / 4.0;
+    f[10] = (r[1] - r[11] - r[13] - r[16] - r[17]) / 2.0 + (r[4] + 2.0 * r[5] + r[6]) * CS2 / 2.0;
+    f[11] = (r[2] - r[10] - r[15] - r[16] - r[18]) / 2.0 + (r[4] + r[6] - r[5]) * CS2 / 2.0;
+    f[12] = (r[3] - r[12] - r[14] - r[17] - r[18]) / 2.0 + (r[4] - r[5] - 2.0 * r[6]) * CS2 / 2.0;
+    f[13] = (r[7] + r[10] + r[11] + r[16]) / 4.0;
+    f[14] = (r[11] + r[16] - r[7] - r[10]) / 4.0;
+    f[15] = (r[8] + r[12] + r[13] + r[17]) / 4.0;
+    f[16] = (r[13] + r[17] - r[8] - r[12]) / 4.0;
+    f[17] = (r[9] + r[14] + r[15] + r[18]) / 4.0;
+    f[18] = (r[15] + r[18] - r[9] - r[14]) / 4.0;
+}
+
 /* App. C two-step reconstruction.  r* = N^-1 k* (Eq. rawQ19), then
  * f* = M^-1 r* (Eq. pdfQ19).  Corrections to the printed text:
  *   r16*: the k5* term carries c_s^2, (2uy^2 - ux^2) k5* cs^2;
@@ -417,25 +441,73 @@ void orc_back_transform(double rho, double ux, double uy, double uz, const doubl
             (-y2 - z2) * k[5] * CS2 + (z2 - 2.0 * y2) * k[6] * CS2 + 4.0 * uy * uz * k[9] + 2.0 * uz * k[14] +
             2.0 * uy * k[15] + k[18];
 
-    f[0] = r[0] - r[4] + r[16] + r[17] + r[18];
-    f[1] = (r[11] + r[13] - r[1] - r[16] - r[17]) / 2.0 + (r[4] + 2.0 * r[5] + r[6]) * CS2 / 2.0;
-    f[2] = (r[10] + r[15] - r[2] - r[16] - r[18]) / 2.0 + (r[4] + r[6] - r[5]) * CS2 / 2.0;
-    f[3] = (r[12] + r[14] - r[3] - r[17] - r[18]) / 2.0 + (r[4] - r[5] - 2.0 * r[6]) * CS2 / 2.0;
-    f[4] = (r[7] + r[16] - r[10] - r[11]) / 4.0;
-    f[5] = (r[10] + r[16] - r[7] - r[11]) / 4.0;
-    f[6] = (r[8] + r[17] - r[12] - r[13]) / 4.0;
-    f[7] = (r[12] + r[17] - r[8] - r[13]) / 4.0;
-    f[8] = (r[9] + r[18] - r[14] - r[15]) / 4.0;
-    f[9] = (r[14] + r[18] - r[9] - r[15]) / 4.0;
-    f[10] = (r[1] - r[11] - r[13] - r[16] - r[17]) / 2.0 + (r[4] + 2.0 * r[5] + r[6]) * CS2 / 2.0;
-    f[11] = (r[2] - r[10] - r[15] - r[16] - r[18]) / 2.0 + (r[4] + r[6] - r[5]) * CS2 / 2.0;
-    f[12] = (r[3] - r[12] - r[14] - r[17] - r[18]) / 2.0 + (r[4] - r[5] - 2.0 * r[6]) * CS2 / 2.0;
-    f[13] = (r[7] + r[10] + r[11] + r[16]) / 4.0;
-    f[14] = (r[11] + r[16] - r[7] - r[10]) / 4.0;
-    f[15] = (r[8] + r[12] + r[13] + r[17]) / 4.0;
-    f[16] = (r[13] + r[17] - r[8] - r[12]) / 4.0;
-    f[17] = (r[9] + r[14] + r[15] + r[18]) / 4.0;
-    f[18] = (r[15] + r[18] - r[9] - r[14]) / 4.0;
+    raw_to_populations(r, f);
+}
+
+/* App. C, raw-moment variant (N = I, T = M): the printed post-collision list
+ *   k0* = rho, k1..3* = rho u + F/2, k4* = rho (3 cs^2 + |u|^2),
+ *   k5..9* = (1 - omega) k5..9 + omega k5..9_eq (raw second moments of f),
+ *   k10* = Fy cs^2/2 + rho uy (ux^2 + cs^2), ... (third order at equilibrium
+ *   plus cs^2 F/2), k16..18* = rho (ua^2 + cs^2)(ub^2 + cs^2),
+ * with r* = k*, then f* = M^-1 r*.  Unlike the central form, the printed list
+ * carries no velocity-dependent forcing terms at second and higher order; with
+ * F = 0 it is the raw-moment MRT with the same relaxation matrix. */
+void orc_kstar_rm(const double *f, double rho, double ux, double uy, double uz, double Fx, double Fy, double Fz,
+                  double omega, double *ks)
+{
+    double k5 = 0, k6 = 0, k7 = 0, k8 = 0, k9 = 0;
+    for (int i = 0; i < Q; i++) {
+        k5 += f[i] * (CX[i] * CX[i] - CY[i] * CY[i]);
+        k6 += f[i] * (CY[i] * CY[i] - CZ[i] * CZ[i]);
+        k7 += f[i] * CX[i] * CY[i];
+        k8 += f[i] * CX[i] * CZ[i];
+        k9 += f[i] * CY[i] * CZ[i];
+    }
+    double x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
+    ks[0] = rho;
+    ks[1] = Fx / 2.0 + rho * ux;
+    ks[2] = Fy / 2.0 + rho * uy;
+    ks[3] = Fz / 2.0 + rho * uz;
+    ks[4] = rho * (3.0 * CS2 + x2 + y2 + z2);
+    ks[5] = (1.0 - omega) * k5 + omega * rho * (x2 - y2);
+    ks[6] = (1.0 - omega) * k6 + omega * rho * (y2 - z2);
+    ks[7] = (1.0 - omega) * k7 + omega * rho * ux * uy;
+    ks[8] = (1.0 - omega) * k8 + omega * rho * ux * uz;
+    ks[9] = (1.0 - omega) * k9 + omega * rho * uy * uz;
+    ks[10] = Fy * CS2 / 2.0 + rho * uy * (x2 + CS2);
+    ks[11] = Fx * CS2 / 2.0 + rho * ux * (y2 + CS2);
+    ks[12] = Fz * CS2 / 2.0 + rho * uz * (x2 + CS2);
+    ks[13] = Fx * CS2 / 2.0 + rho * ux * (z2 + CS2);
+    ks[14] = Fz * CS2 / 2.0 + rho * uz * (y2 + CS2);
+    ks[15] = Fy * CS2 / 2.0 + rho * uy * (z2 + CS2);
+    ks[16] = rho * (x2 + CS2) * (y2 + CS2);
+    ks[17] = rho * (x2 + CS2) * (z2 + CS2);
+    ks[18] = rho * (y2 + CS2) * (z2 + CS2);
+}
+
+void orc_collide_rm(const double *f, double rho, double ux, double uy, double uz, double Fx, double Fy, double Fz,
+                    double omega, double *fout)
+{
+    double ks[Q];
+    orc_kstar_rm(f, rho, ux, uy, uz, Fx, Fy, Fz, omega, ks);
+    raw_to_populations(ks, fout);
+}
+
+/* The raw-moment MRT by definition: k = M f, k_eq = M f_eq, R = M F_i with the
+ * printed raw forcing moments (App. B), k* = (I - K) k + K k_eq + (I - K/2) R,
+ * then M f* = k* solved; M = T(0) (App. C). */
+int orc_collide_dense_rm(const double *f, double rho, double ux, double uy, double uz, double Fx, double Fy, double Fz,
+                         double omega, double *fout)
+{
+    double M[Q * Q], k[Q], keq[Q], R[Q], ks[Q], feq[Q], Kd[Q];
+    orc_T(0.0, 0.0, 0.0, M);
+    matvec(M, f, k);
+    orc_feq(rho, ux, uy, uz, feq);
+    matvec(M, feq, keq);
+    orc_forcing_rm(ux, uy, uz, Fx, Fy, Fz, R);
+    for (int r = 0; r < Q; r++) Kd[r] = (r >= 5 && r <= 9) ? omega : 1.0;
+    for (int r = 0; r < Q; r++) ks[r] = (1.0 - Kd[r]) * k[r] + Kd[r] * keq[r] + (1.0 - 0.5 * Kd[r]) * R[r];
+    return orc_solve19(M, ks, fout);
 }
 
 int orc_collide_closed(const double *f, double rho, double ux, double uy, double uz, double Fx, double Fy,
@@ -522,6 +594,7 @@ typedef struct {
     double G; /* Shan-Chen interaction strength (physics 3) */
     double rho_ref; /* body force F = (rho - rho_ref) g (Sec. III.H uses the mean density) */
     int wall_model; /* 0: half-way bounce-back; 1: regularized on-node walls on the y axis */
+    int raw_moments; /* 1: the raw-moment variant of App. C (N = I) instead of central moments */
 } orc_params;
 
 static long cell_index(const orc_params *p, int x, int y, int z)
@@ -740,6 +813,14 @@ static void node_macro(const orc_params *p, const double *fin, const double *gin
 static int collide(const orc_params *p, const double *fin, const node_state *s, int cgm, double alpha,
                    double *fout)
 {
+    if (p->raw_moments && !cgm) {
+        if (p->closed_form) {
+            orc_collide_rm(fin, s->rho, s->u[0], s->u[1], s->u[2], s->F[0], s->F[1], s->F[2], p->omega, fout);
+            return 0;
+        }
+        return orc_collide_dense_rm(fin, s->rho, s->u[0], s->u[1], s->u[2], s->F[0], s->F[1], s->F[2], p->omega,
+                                    fout);
+    }
     if (p->closed_form)
         return orc_collide_closed(fin, s->rho, s->u[0], s->u[1], s->u[2], s->F[0], s->F[1], s->F[2], p->omega, cgm,
                                   alpha, fout);
