@@ -229,6 +229,8 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
         out.update(_sc(L, timed, steps, peak, (n_only,) if n_only else (100, 256)))
     if only in (None, "rt"):
         out.update(_rt(L, timed, steps, peak))
+    if only in (None, "appd"):
+        out.update(_appd(L, timed, steps, n_only or 256))
     if only in (None, "channel"):
         out.update(_channel(L, timed, steps, peak, n_only or 512))
     return out
@@ -352,6 +354,29 @@ def _rt(L, timed, steps, peak):
         "MLUPS": cells * n_c / t / 1e6, "steps": n_c, "bytes_per_lup": 312, "moved_bytes_per_lup": 464,
         "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
         "note": "colour-gradient two-pass step with walls; 312 B/LUP algorithmic"}}
+
+
+def _appd(L, timed, steps, n=256):
+    # App. D's timing comparison on its workload, the 3D Taylor-Green vortex (Sec. III.E, u0 = 0.05, tau = 0.53):
+    # raw- against central-moment collision, D3Q19, FP32 (HBM-bound) and FP64 (FP64-ALU-bound), n^3.
+    rho, u = inputs.taylor_green_3d(n, u0=0.05)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        row = {}
+        for coll in ("rm", "cm"):
+            c = L.lbm_create((n, n, n), 1 / 0.53, precision=prec, collision=coll)
+            L.lbm_init_fields(c, rho, u)
+            L.lbm_set_launch_shape(c, 0, 256, 0, 1)
+            L.lbm_step(c, 3)
+            k = max(20, steps // (4 if prec == "fp32" else 20))
+            t = timed(lambda m: L.lbm_step(c, m), k)
+            L.lbm_destroy(c)
+            row[f"Q19-{coll.upper()}"] = {"MLUPS": n ** 3 * k / t / 1e6, "steps": k}
+        row["CM_over_RM_time"] = row["Q19-RM"]["MLUPS"] / row["Q19-CM"]["MLUPS"]
+        out[prec] = row
+    out["note"] = ("direct kernel, one node per thread; the paper's CPU ratio CM/RM time is 1.04-1.07 (Table of "
+                   "App. D)")
+    return {f"appD_timing_taylor_green_{n}": out}
 
 
 def _channel(L, timed, steps, peak, n=512):
@@ -557,7 +582,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "sc", "rt", "channel", "fma-probe"], default=None,
+    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "sc", "rt", "channel", "appd", "fma-probe"],
+                    default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     ap.add_argument("--launch", default="auto",

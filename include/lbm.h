@@ -88,12 +88,20 @@ typedef struct {
     int wall_model;         /* lbm_wall_model */
 } lbm_grid;
 
+/* Moment space of the collision.  LBM_MOMENTS_CENTRAL: the paper's central
+ * moments (Sec. II.B).  LBM_MOMENTS_RAW: the raw-moment variant of App. C
+ * (N = I, the printed post-collision list; its forcing enters at first and
+ * third order only), single phase with half-way bounce-back walls, direct
+ * launch shape only. */
+typedef enum { LBM_MOMENTS_CENTRAL = 0, LBM_MOMENTS_RAW = 1 } lbm_moment_space;
+
 /* Diagonal relaxation matrix K of Sec. II.B: omega on the five deviatoric
  * second-order CMs; omega_bulk on the trace (k4); omega_3 on k10..k15;
  * omega_4 on k16..k18.  The paper sets omega_bulk = omega_3 = omega_4 = 1,
  * the only values this build accepts (others give LBM_ERR_UNSUPPORTED). */
 typedef struct {
     double omega, omega_bulk, omega_3, omega_4;
+    int moment_space; /* lbm_moment_space */
 } lbm_relax;
 
 /* Body force F = (rho - rho_ref) g (Eq. eq:posColl0): a constant acceleration

@@ -23,6 +23,7 @@ LBM_D3Q19 = 0
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 PHYSICS = {"fluid": 0, "mhd": 1, "cgm": 2, "sc": 3}
 WALL_MODELS = {"bounce_back": 0, "regularized": 1}
+MOMENT_SPACES = {"cm": 0, "rm": 1}
 
 if not os.path.exists(_build.LIB):
     raise ImportError(f"liblbm.so is not built ({_build.LIB}); run paper_2010_01628_gb300.build.build() first")
@@ -37,7 +38,7 @@ class lbm_grid(ctypes.Structure):
 
 class lbm_relax(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("omega_bulk", ctypes.c_double), ("omega_3", ctypes.c_double),
-                ("omega_4", ctypes.c_double)]
+                ("omega_4", ctypes.c_double), ("moment_space", ctypes.c_int)]
 
 
 class lbm_forcing(ctypes.Structure):
@@ -156,13 +157,14 @@ def _ptr(a, n_expected=None, writable=False):
 
 def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0,
-               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0, wall_model="bounce_back", omega_bulk=1.0,
-               omega_3=1.0, omega_4=1.0, stream=None):
+               alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0, wall_model="bounce_back", collision="cm",
+               omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
     """Create a context; returns its handle (an int).  shape = (nx, ny, nz).
     physics: "fluid", "mhd" (tau_m, b_wall), "cgm" (alpha_r, alpha_b, A, beta)
     or "sc" (Shan-Chen, interaction strength G).  The body force is
     F = (rho - rho_ref) g (rho_ref != 0: two-phase modules only).  wall_model:
-    "bounce_back" (half-way) or "regularized" (on-node walls on y, single phase)."""
+    "bounce_back" (half-way) or "regularized" (on-node walls on y, single phase).
+    collision: "cm" (central moments) or "rm" (the raw-moment variant, single phase)."""
     if _alloc_refs is None and _torch() is not None:
         lbm_set_allocator(True)
     gr = lbm_grid()
@@ -171,7 +173,7 @@ def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.
     for a in range(3):
         gr.lid_u[a] = float(lid_u[a])
     gr.wall_model = WALL_MODELS[wall_model]
-    rl = lbm_relax(float(omega), float(omega_bulk), float(omega_3), float(omega_4))
+    rl = lbm_relax(float(omega), float(omega_bulk), float(omega_3), float(omega_4), MOMENT_SPACES[collision])
     fo = lbm_forcing()
     for a in range(3):
         fo.g[a] = float(g[a])

@@ -332,7 +332,8 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
             return LBM_ERR_UNSUPPORTED;
         if (physics == LBM_PHYS_MHD && !(phys[d].tau_m > 0.5)) return LBM_ERR_ARG;
         if (forcing && forcing[d].rho_ref != 0.0) return LBM_ERR_UNSUPPORTED;
-        if (g.wall_model != LBM_WALL_BOUNCE_BACK) return LBM_ERR_UNSUPPORTED;
+        if (g.wall_model != LBM_WALL_BOUNCE_BACK || relax[d].moment_space != LBM_MOMENTS_CENTRAL)
+            return LBM_ERR_UNSUPPORTED;
         if (physics == LBM_PHYS_MHD && (g.periodic_mask & 2u) == 0 &&
             (g.lid_u[0] != 0.0 || g.lid_u[1] != 0.0 || g.lid_u[2] != 0.0))
             return LBM_ERR_UNSUPPORTED;

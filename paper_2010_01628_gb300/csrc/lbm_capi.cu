@@ -223,6 +223,10 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     }
     if (physics == LBM_PHYS_SC && !std::isfinite(phys->G)) return LBM_ERR_ARG;
     if (grid->wall_model != LBM_WALL_BOUNCE_BACK && grid->wall_model != LBM_WALL_REGULARIZED) return LBM_ERR_ARG;
+    if (relax->moment_space != LBM_MOMENTS_CENTRAL && relax->moment_space != LBM_MOMENTS_RAW) return LBM_ERR_ARG;
+    if (relax->moment_space == LBM_MOMENTS_RAW &&
+        (physics != LBM_PHYS_FLUID || grid->wall_model != LBM_WALL_BOUNCE_BACK))
+        return LBM_ERR_UNSUPPORTED;
     if (grid->wall_model == LBM_WALL_REGULARIZED &&
         (physics != LBM_PHYS_FLUID || (grid->periodic_mask & 7u) != 5u || grid->ny < 3))
         return LBM_ERR_UNSUPPORTED;

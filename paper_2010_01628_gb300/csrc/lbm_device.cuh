@@ -258,6 +258,36 @@ __device__ __forceinline__ void conserve_mass(C (&f)[Q], C drho) {
     f[0] = drho - moments19(f).moving;
 }
 
+// f = M^-1 r (App. C, Eq. pdfQ19): populations from the 19 raw moments.
+template <typename C>
+__device__ __forceinline__ void raw_to_populations(const C (&r)[Q], C (&f)[Q]) {
+    const C half = (C)0.5, quarter = (C)0.25, sixth = (C)(1.0 / 6.0);
+    const C ax = (r[4] + (C)2 * r[5] + r[6]) * sixth;
+    const C ay = (r[4] - r[5] + r[6]) * sixth;
+    const C az = (r[4] - r[5] - (C)2 * r[6]) * sixth;
+    const C s1617 = r[16] + r[17], s1618 = r[16] + r[18], s1718 = r[17] + r[18];
+    f[0] = r[0] - r[4] + r[16] + s1718;
+    const C bx = (r[11] + r[13]) * half, by = (r[10] + r[15]) * half, bz = (r[12] + r[14]) * half;
+    f[1] = bx - (r[1] + s1617) * half + ax;
+    f[10] = -bx + (r[1] - s1617) * half + ax;
+    f[2] = by - (r[2] + s1618) * half + ay;
+    f[11] = -by + (r[2] - s1618) * half + ay;
+    f[3] = bz - (r[3] + s1718) * half + az;
+    f[12] = -bz + (r[3] - s1718) * half + az;
+    f[4] = (r[7] + r[16] - r[10] - r[11]) * quarter;
+    f[5] = (r[10] + r[16] - r[7] - r[11]) * quarter;
+    f[13] = (r[7] + r[10] + r[11] + r[16]) * quarter;
+    f[14] = (r[11] + r[16] - r[7] - r[10]) * quarter;
+    f[6] = (r[8] + r[17] - r[12] - r[13]) * quarter;
+    f[7] = (r[12] + r[17] - r[8] - r[13]) * quarter;
+    f[15] = (r[8] + r[12] + r[13] + r[17]) * quarter;
+    f[16] = (r[13] + r[17] - r[8] - r[12]) * quarter;
+    f[8] = (r[9] + r[18] - r[14] - r[15]) * quarter;
+    f[9] = (r[14] + r[18] - r[9] - r[15]) * quarter;
+    f[17] = (r[9] + r[14] + r[15] + r[18]) * quarter;
+    f[18] = (r[15] + r[18] - r[9] - r[14]) * quarter;
+}
+
 // ---------------------------------------------------------------------------
 // Back-transform of App. C in two steps, r* = N^-1 k* (Eq. rawQ19) then
 // f* = M^-1 r* (Eq. pdfQ19), for a post-collision CM vector with
@@ -308,31 +338,7 @@ __device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C 
     r[17] = z2 * (rx2 + Ax) + x2 * Az + tx * (tz * k8 + t[3]) + tz * t[2] + k17c;
     r[18] = z2 * (ry2 + Ay) + y2 * Az + ty * (tz * k9 + t[5]) + tz * t[4] + k18c;
 
-    const C half = (C)0.5, quarter = (C)0.25, sixth = (C)(1.0 / 6.0);
-    const C ax = (r[4] + (C)2 * r[5] + r[6]) * sixth;
-    const C ay = (r[4] - r[5] + r[6]) * sixth;
-    const C az = (r[4] - r[5] - (C)2 * r[6]) * sixth;
-    const C s1617 = r[16] + r[17], s1618 = r[16] + r[18], s1718 = r[17] + r[18];
-    f[0] = r[0] - r[4] + r[16] + s1718;
-    const C bx = (r[11] + r[13]) * half, by = (r[10] + r[15]) * half, bz = (r[12] + r[14]) * half;
-    f[1] = bx - (r[1] + s1617) * half + ax;
-    f[10] = -bx + (r[1] - s1617) * half + ax;
-    f[2] = by - (r[2] + s1618) * half + ay;
-    f[11] = -by + (r[2] - s1618) * half + ay;
-    f[3] = bz - (r[3] + s1718) * half + az;
-    f[12] = -bz + (r[3] - s1718) * half + az;
-    f[4] = (r[7] + r[16] - r[10] - r[11]) * quarter;
-    f[5] = (r[10] + r[16] - r[7] - r[11]) * quarter;
-    f[13] = (r[7] + r[10] + r[11] + r[16]) * quarter;
-    f[14] = (r[11] + r[16] - r[7] - r[10]) * quarter;
-    f[6] = (r[8] + r[17] - r[12] - r[13]) * quarter;
-    f[7] = (r[12] + r[17] - r[8] - r[13]) * quarter;
-    f[15] = (r[8] + r[12] + r[13] + r[17]) * quarter;
-    f[16] = (r[13] + r[17] - r[8] - r[12]) * quarter;
-    f[8] = (r[9] + r[18] - r[14] - r[15]) * quarter;
-    f[9] = (r[14] + r[18] - r[9] - r[15]) * quarter;
-    f[17] = (r[9] + r[14] + r[15] + r[18]) * quarter;
-    f[18] = (r[15] + r[18] - r[9] - r[14]) * quarter;
+    raw_to_populations<C>(r, f);
 }
 
 // 1/x: correctly rounded reciprocal (the FP32 division would add a slow path).
@@ -366,6 +372,44 @@ __device__ __forceinline__ void collide_fluid(C (&f)[Q], const Moments<C>& m, co
     const C drho = m.drho;
     const C k16c = drho * (C)(1.0 / 9.0);
     back_transform<C>(rho, ux, uy, uz, hx, hy, hz, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+}
+
+// Raw-moment variant (App. C, N = I, T = M): r* = k* from the printed list, in
+// the shifted variables (the rest state's raw moments r0 = 1, r4 = 3 c_s^2 = 1,
+// r16..18 = c_s^4 = 1/9 subtracted exactly), then f* = M^-1 r*.
+//   r1..3* = rho u + F/2; r4* = rho (3 c_s^2 + |u|^2);
+//   r5..9* = (1 - omega) r5..9 + omega rho (u u)_5..9;
+//   r10..15* = c_s^2 F/2 + rho u_b (u_a^2 + c_s^2); r16..18* = rho (u_a^2 + c_s^2)(u_b^2 + c_s^2).
+template <typename C>
+__device__ __forceinline__ void collide_fluid_rm(C (&f)[Q], const Moments<C>& m, const Macro<C>& a, C omega) {
+    const C rho = a.rho, ux = a.ux, uy = a.uy, uz = a.uz;
+    const C hx = (C)0.5 * a.Fx, hy = (C)0.5 * a.Fy, hz = (C)0.5 * a.Fz;
+    const C x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
+    const C om1 = (C)1 - omega, third = (C)(1.0 / 3.0), ninth = (C)(1.0 / 9.0);
+    const C drho = m.drho;
+    C r[Q];
+    r[0] = drho;
+    r[1] = rho * ux + hx;
+    r[2] = rho * uy + hy;
+    r[3] = rho * uz + hz;
+    r[4] = drho + rho * (x2 + y2 + z2);
+    r[5] = om1 * m.pxx_m_pyy + omega * rho * (x2 - y2);
+    r[6] = om1 * m.pyy_m_pzz + omega * rho * (y2 - z2);
+    r[7] = om1 * m.pxy + omega * rho * ux * uy;
+    r[8] = om1 * m.pxz + omega * rho * ux * uz;
+    r[9] = om1 * m.pyz + omega * rho * uy * uz;
+    const C ax = x2 + third, ay = y2 + third, az = z2 + third;
+    const C rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
+    r[10] = hy * third + ruy * ax;
+    r[11] = hx * third + rux * ay;
+    r[12] = hz * third + ruz * ax;
+    r[13] = hx * third + rux * az;
+    r[14] = hz * third + ruz * ay;
+    r[15] = hy * third + ruy * az;
+    r[16] = rho * (x2 * y2 + (x2 + y2) * third) + drho * ninth;
+    r[17] = rho * (x2 * z2 + (x2 + z2) * third) + drho * ninth;
+    r[18] = rho * (y2 * z2 + (y2 + z2) * third) + drho * ninth;
+    raw_to_populations<C>(r, f);
 }
 
 // Equilibrium of (rho, u) in shifted form: the back-transform of k_eq.

@@ -13,12 +13,12 @@
 
 namespace lbm {
 
-template <typename S, typename C, bool WALLS>
+template <typename S, typename C, bool WALLS, bool RM = false>
 __global__ void __launch_bounds__(256) fluid_step_kernel(const S* __restrict__ src, S* __restrict__ dst,
                                                          FluidArgs p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.box.nx) return;
-    fluid_node<S, C, WALLS, true>(src, dst, p, x, blockIdx.y, blockIdx.z);
+    fluid_node<S, C, WALLS, true, RM>(src, dst, p, x, blockIdx.y, blockIdx.z);
 }
 
 // Channels (x and z periodic, walls on y, ny >= 3) step in two launches: the
@@ -409,7 +409,9 @@ static size_t tma_smem_bytes(const lbm_ctx* c, int stages) {
 }
 
 int fluid_tma_max_stages(const lbm_ctx* c, int ctas) {
-    if (c->physics != LBM_PHYS_FLUID || c->grid.wall_model != LBM_WALL_BOUNCE_BACK || ctas < 1 || ctas > 4) return 0;
+    if (c->physics != LBM_PHYS_FLUID || c->grid.wall_model != LBM_WALL_BOUNCE_BACK ||
+        c->relax.moment_space != LBM_MOMENTS_CENTRAL || ctas < 1 || ctas > 4)
+        return 0;
     if (((size_t)c->box.nx * c->elem) % 16 != 0 || c->box.nx < 32) return 0;
     const size_t budget = (ctas == 1 ? SMEM_PER_BLOCK_OPTIN : SMEM_PER_SM / (size_t)ctas - 1024) - 256;
     int st = 0;
@@ -447,6 +449,19 @@ static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const FluidArgs p = fluid_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
+    if (c->relax.moment_space == LBM_MOMENTS_RAW) {
+        const dim3 grid = step_grid(c->box, bx);
+        for (long s = 0; s < n; ++s) {
+            const S* src = (const S*)c->buf[c->cur];
+            S* dst = (S*)c->buf[c->cur ^ 1];
+            if (walls)
+                fluid_step_kernel<S, C, true, true><<<grid, bx, 0, c->stream>>>(src, dst, p);
+            else
+                fluid_step_kernel<S, C, false, true><<<grid, bx, 0, c->stream>>>(src, dst, p);
+            if (!dry) c->cur ^= 1;
+        }
+        return cudaGetLastError();
+    }
     const bool reg = c->grid.wall_model == LBM_WALL_REGULARIZED;
     const bool channel = (c->box.periodic & 7u) == 5u && c->box.ny >= 3;
     if (channel && (reg || c->variant == 0)) {

@@ -93,8 +93,9 @@ __device__ __forceinline__ void gather_regularized(const S* __restrict__ src, co
 }
 
 // One node: pull (stream + boundaries), moments, forced CM collision, store.
-// NC selects the read-only load path (sources not written during the kernel).
-template <typename S, typename C, bool WALLS, bool NC>
+// NC selects the read-only load path (sources not written during the kernel);
+// RM the raw-moment variant of App. C.
+template <typename S, typename C, bool WALLS, bool NC, bool RM = false>
 __device__ __forceinline__ void fluid_node(const S* __restrict__ src, S* __restrict__ dst, const FluidArgs& p, int x,
                                            int y, int z) {
     const Box& b = p.box;
@@ -104,7 +105,10 @@ __device__ __forceinline__ void fluid_node(const S* __restrict__ src, S* __restr
     gather19<S, C, WALLS, NC>(src, b, q, x, y, z, self, (C)p.lid[0], (C)p.lid[1], (C)p.lid[2], f);
     const Moments<C> m = moments19(f);
     const Macro<C> a = fluid_macro(m, (C)p.g[0], (C)p.g[1], (C)p.g[2]);
-    collide_fluid<C>(f, m, a, (C)p.omega);
+    if (RM)
+        collide_fluid_rm<C>(f, m, a, (C)p.omega);
+    else
+        collide_fluid<C>(f, m, a, (C)p.omega);
     scatter19<S, C>(dst, b.n, self, f);
 }
 
