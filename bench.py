@@ -363,19 +363,21 @@ def _appd(L, timed, steps, n=256):
     out = {}
     for prec in ("fp32", "fp64"):
         row = {}
-        for coll in ("rm", "cm"):
-            c = L.lbm_create((n, n, n), 1 / 0.53, precision=prec, collision=coll)
-            L.lbm_init_fields(c, rho, u)
-            L.lbm_set_launch_shape(c, 0, 256, 0, 1)
-            L.lbm_step(c, 3)
-            k = max(20, steps // (4 if prec == "fp32" else 20))
-            t = timed(lambda m: L.lbm_step(c, m), k)
-            L.lbm_destroy(c)
-            row[f"Q19-{coll.upper()}"] = {"MLUPS": n ** 3 * k / t / 1e6, "steps": k}
-        row["CM_over_RM_time"] = row["Q19-RM"]["MLUPS"] / row["Q19-CM"]["MLUPS"]
+        for lat in ("d3q19", "d3q27"):
+            for coll in ("rm", "cm"):
+                c = L.lbm_create((n, n, n), 1 / 0.53, precision=prec, collision=coll, lattice=lat)
+                L.lbm_init_fields(c, rho, u)
+                L.lbm_set_launch_shape(c, 0, 256, 0, 1)
+                L.lbm_step(c, 3)
+                k = max(20, steps // (4 if prec == "fp32" else 20))
+                t = timed(lambda m: L.lbm_step(c, m), k)
+                L.lbm_destroy(c)
+                row[f"Q{lat[-2:]}-{coll.upper()}"] = {"MLUPS": n ** 3 * k / t / 1e6, "steps": k}
+        base = row["Q19-RM"]["MLUPS"]
+        row["time_relative_to_Q19-RM"] = {key: base / v["MLUPS"] for key, v in row.items()}
         out[prec] = row
-    out["note"] = ("direct kernel, one node per thread; the paper's CPU ratio CM/RM time is 1.04-1.07 (Table of "
-                   "App. D)")
+    out["note"] = ("direct kernels, one node per thread; the paper's CPU times relative to Q19-RM at D = 128: "
+                   "Q19-CM 1.06, Q27-RM 1.53, Q27-CM 1.82 (Table of App. D)")
     return {f"appD_timing_taylor_green_{n}": out}
 
 

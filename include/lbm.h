@@ -53,7 +53,11 @@ typedef enum {
     LBM_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
 } lbm_status;
 
-typedef enum { LBM_D3Q19 = 0 } lbm_lattice;
+/* Velocity sets.  LBM_D3Q19: the paper's lattice (Sec. II.A).  LBM_D3Q27: the
+ * App. D lattice (single phase, FP64 or FP32, half-way bounce-back walls,
+ * central or raw moments, direct launch shape), used for the App. D cost
+ * comparison. */
+typedef enum { LBM_D3Q19 = 0, LBM_D3Q27 = 1 } lbm_lattice;
 
 /* Population storage.  FP64 and FP32 store f_i - w_i (shifted by the rest
  * equilibrium of rho0 = 1) and compute in their own type.  The 16-bit formats

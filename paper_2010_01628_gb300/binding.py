@@ -158,13 +158,14 @@ def _ptr(a, n_expected=None, writable=False):
 def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0,
                alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0, wall_model="bounce_back", collision="cm",
-               omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
+               lattice="d3q19", omega_bulk=1.0, omega_3=1.0, omega_4=1.0, stream=None):
     """Create a context; returns its handle (an int).  shape = (nx, ny, nz).
     physics: "fluid", "mhd" (tau_m, b_wall), "cgm" (alpha_r, alpha_b, A, beta)
     or "sc" (Shan-Chen, interaction strength G).  The body force is
     F = (rho - rho_ref) g (rho_ref != 0: two-phase modules only).  wall_model:
     "bounce_back" (half-way) or "regularized" (on-node walls on y, single phase).
-    collision: "cm" (central moments) or "rm" (the raw-moment variant, single phase)."""
+    collision: "cm" (central moments) or "rm" (the raw-moment variant, single phase).
+    lattice: "d3q19" or "d3q27" (single phase, FP32/FP64)."""
     if _alloc_refs is None and _torch() is not None:
         lbm_set_allocator(True)
     gr = lbm_grid()
@@ -186,7 +187,8 @@ def lbm_create(shape, omega, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.
     ph.G = float(G)
     ctx = _V()
     s = _current_stream() if stream is None else int(stream)
-    _check(_lib.lbm_create(ctypes.byref(ctx), ctypes.byref(gr), LBM_D3Q19, ctypes.byref(rl), ctypes.byref(fo),
+    _check(_lib.lbm_create(ctypes.byref(ctx), ctypes.byref(gr), {"d3q19": 0, "d3q27": 1}[lattice], ctypes.byref(rl),
+                           ctypes.byref(fo),
                            PHYSICS[physics], ctypes.byref(ph), PRECISIONS[precision], _V(s)))
     return ctx.value
 

@@ -67,6 +67,7 @@ int slab_planes(const lbm_ctx* c) {
 }
 
 cudaError_t phys_step(lbm_ctx* c, long n, bool dry = false) {
+    if (c->q == 27) return lbm::q27_step(c, n, dry);
     switch (c->physics) {
         case LBM_PHYS_FLUID: return lbm::fluid_step(c, n, dry);
         case LBM_PHYS_MHD: return lbm::mhd_step(c, n, dry);
@@ -76,6 +77,7 @@ cudaError_t phys_step(lbm_ctx* c, long n, bool dry = false) {
     return cudaErrorInvalidValue;
 }
 cudaError_t phys_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform) {
+    if (c->q == 27) return lbm::q27_init(c, slab, z0, nzs, uniform);
     switch (c->physics) {
         case LBM_PHYS_FLUID: return lbm::fluid_init(c, slab, z0, nzs, uniform);
         case LBM_PHYS_MHD: return lbm::mhd_init(c, slab, z0, nzs, uniform);
@@ -85,6 +87,7 @@ cudaError_t phys_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool unif
     return cudaErrorInvalidValue;
 }
 cudaError_t phys_fields(lbm_ctx* c, double* slab, int z0, int nzs) {
+    if (c->q == 27) return lbm::q27_fields(c, slab, z0, nzs);
     switch (c->physics) {
         case LBM_PHYS_FLUID: return lbm::fluid_fields(c, slab, z0, nzs);
         case LBM_PHYS_MHD: return lbm::mhd_fields(c, slab, z0, nzs);
@@ -94,6 +97,7 @@ cudaError_t phys_fields(lbm_ctx* c, double* slab, int z0, int nzs) {
     return cudaErrorInvalidValue;
 }
 cudaError_t phys_reduce(lbm_ctx* c, bool record) {
+    if (c->q == 27) return lbm::q27_reduce(c, record);
     switch (c->physics) {
         case LBM_PHYS_FLUID: return lbm::fluid_reduce(c, record);
         case LBM_PHYS_MHD: return lbm::mhd_reduce(c, record);
@@ -202,7 +206,11 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
                       lbm_precision precision, void* cuda_stream) {
     if (!out || !grid || !relax) return LBM_ERR_ARG;
     *out = nullptr;
-    if (lattice != LBM_D3Q19) return LBM_ERR_UNSUPPORTED;
+    if (lattice != LBM_D3Q19 && lattice != LBM_D3Q27) return LBM_ERR_UNSUPPORTED;
+    if (lattice == LBM_D3Q27 &&
+        (physics != LBM_PHYS_FLUID || (precision != LBM_FP32 && precision != LBM_FP64) ||
+         grid->wall_model != LBM_WALL_BOUNCE_BACK || (forcing && forcing->rho_ref != 0.0)))
+        return LBM_ERR_UNSUPPORTED;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->ny > 65535 || grid->nz > 65535) return LBM_ERR_ARG;
     const double cells = (double)grid->nx * grid->ny * grid->nz;
     if (cells >= 2147483648.0) return LBM_ERR_ARG;
@@ -260,7 +268,9 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->box.periodic = grid->periodic_mask & 7u;
     c->box.n = (size_t)grid->nx * grid->ny * grid->nz;
     c->elem = precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
-    c->planes = (physics == LBM_PHYS_FLUID || physics == LBM_PHYS_SC) ? 19 : (physics == LBM_PHYS_MHD ? 40 : 38);
+    c->q = lattice == LBM_D3Q27 ? 27 : 19;
+    c->planes = c->q == 27 ? 27
+                           : ((physics == LBM_PHYS_FLUID || physics == LBM_PHYS_SC) ? 19 : (physics == LBM_PHYS_MHD ? 40 : 38));
     c->alloc = g_alloc;
     c->release = g_release;
     c->user = g_user;

@@ -409,7 +409,7 @@ static size_t tma_smem_bytes(const lbm_ctx* c, int stages) {
 }
 
 int fluid_tma_max_stages(const lbm_ctx* c, int ctas) {
-    if (c->physics != LBM_PHYS_FLUID || c->grid.wall_model != LBM_WALL_BOUNCE_BACK ||
+    if (c->physics != LBM_PHYS_FLUID || c->q != 19 || c->grid.wall_model != LBM_WALL_BOUNCE_BACK ||
         c->relax.moment_space != LBM_MOMENTS_CENTRAL || ctas < 1 || ctas > 4)
         return 0;
     if (((size_t)c->box.nx * c->elem) % 16 != 0 || c->box.nx < 32) return 0;

@@ -21,7 +21,8 @@ struct lbm_ctx {
     int device;
     lbm::Box box;
     size_t elem;      // bytes per stored population value
-    int planes;       // stored planes per state copy (19 fluid and Shan-Chen, 40 MHD, 38 CGM)
+    int planes;       // stored planes per state copy (19 fluid and Shan-Chen, 27 D3Q27, 40 MHD, 38 CGM)
+    int q = 19;       // lattice: 19 or 27
     void* buf[2];     // state copies (pull A-B); buf[cur] is current
     int cur;
     void* phi;        // CGM order parameter / Shan-Chen pseudopotential (compute type)
@@ -88,6 +89,12 @@ cudaError_t cgm_step(lbm_ctx* c, long n, bool dry = false);
 cudaError_t cgm_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t cgm_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t cgm_reduce(lbm_ctx* c, bool record);
+
+// D3Q27 single phase (lbm_q27.cu).
+cudaError_t q27_step(lbm_ctx* c, long n, bool dry = false);
+cudaError_t q27_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
+cudaError_t q27_fields(lbm_ctx* c, double* slab, int z0, int nzs);
+cudaError_t q27_reduce(lbm_ctx* c, bool record);
 
 // Shan-Chen (lbm_sc.cu); initialisation is the single-phase one.
 cudaError_t sc_step(lbm_ctx* c, long n, bool dry = false);

@@ -121,10 +121,10 @@ std::string cache_key(const lbm_ctx* c, const std::vector<long>& domain_sizes) {
     if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) dev = prop.name;
     char buf[256];
     if (!c->batch) {
-        std::snprintf(buf, sizeof(buf), "%s|%s|%s|%dx%dx%d|p%u%s%s", dev.c_str(), phys_name(c->physics),
+        std::snprintf(buf, sizeof(buf), "%s|%s|%s|%dx%dx%d|p%u%s%s%s", dev.c_str(), phys_name(c->physics),
                       prec_name(c->prec), c->box.nx, c->box.ny, c->box.nz, c->box.periodic,
                       c->grid.wall_model == LBM_WALL_REGULARIZED ? "|reg" : "",
-                      c->relax.moment_space == LBM_MOMENTS_RAW ? "|rm" : "");
+                      c->relax.moment_space == LBM_MOMENTS_RAW ? "|rm" : "", c->q == 27 ? "|q27" : "");
         return buf;
     }
     unsigned long long h = 1469598103934665603ull;  // FNV-1a over the domain sizes
@@ -162,7 +162,7 @@ extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads,
         if (variant == 2 && !(c->physics == LBM_PHYS_FLUID &&
                               (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) && c->box.nx % 2 == 0 &&
                               c->grid.wall_model == LBM_WALL_BOUNCE_BACK &&
-                              c->relax.moment_space == LBM_MOMENTS_CENTRAL))
+                              c->relax.moment_space == LBM_MOMENTS_CENTRAL && c->q == 19))
             return LBM_ERR_UNSUPPORTED;
         c->variant = variant;
         c->block_x = threads;
@@ -261,7 +261,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
         for (int bx : {64, 128, 256}) cands.push_back({0, bx, 0, 1});
         if (c->physics == LBM_PHYS_FLUID && (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) &&
             c->box.nx % 2 == 0 && c->grid.wall_model == LBM_WALL_BOUNCE_BACK &&
-            c->relax.moment_space == LBM_MOMENTS_CENTRAL)
+            c->relax.moment_space == LBM_MOMENTS_CENTRAL && c->q == 19)
             for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
         for (int ctas : {1, 2, 3, 4}) {
             const int smax = lbm::fluid_tma_max_stages(c, ctas);

@@ -62,7 +62,9 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert create(omega=2.0) == L.LBM_ERR_ARG
     assert create(omega=0.0) == L.LBM_ERR_ARG
     assert create(ob=1.2) == L.LBM_ERR_UNSUPPORTED
-    assert create(lattice=1) == L.LBM_ERR_UNSUPPORTED
+    assert create(lattice=2) == L.LBM_ERR_UNSUPPORTED
+    assert create(lattice=1, precision=2) == L.LBM_ERR_UNSUPPORTED  # D3Q27: FP32/FP64 only
+    assert create(lattice=1, physics=2) == L.LBM_ERR_UNSUPPORTED  # D3Q27: single phase only
     assert create(physics=1, precision=2) == L.LBM_ERR_UNSUPPORTED
     assert create(precision=9) == L.LBM_ERR_ARG
     assert L._lib.lbm_step(None, 1) == L.LBM_ERR_ARG
