@@ -165,6 +165,37 @@ def rayleigh_taylor(W=64, rho_h=3.0, rho_l=1.0, amp=0.05, ny_factor=4):
     return rho, np.zeros((3, nz, ny, nx)), phase
 
 
+def double_shear_layer(L=256, u0=0.57 / math.sqrt(3.0), kappa=80.0, delta=0.05):
+    """Double shear layer (Sec. III.B) on a periodic L x L x 1 box, nodes at
+    x, y = 0 .. L-1: u_x = u0 tanh(kappa (y/L - 1/4)) for y/L <= 1/2, else
+    u0 tanh(kappa (3/4 - y/L)); u_y = u0 delta sin(2 pi (x/L + 1/4)); rho = 1."""
+    x, y, _ = grid(L, L, 1)
+    ux = np.where(y / L <= 0.5, u0 * np.tanh(kappa * (y / L - 0.25)), u0 * np.tanh(kappa * (0.75 - y / L)))
+    uy = u0 * delta * np.sin(2.0 * math.pi * (x / L + 0.25))
+    u = np.stack([ux, uy, np.zeros_like(ux)])
+    return np.ones_like(ux), u
+
+
+def dipole(D_lb, U_lb, inclined=False, w_e=299.56, r0=0.1):
+    """Dipole in the box [-1, 1]^2 (Sec. III.D), 2 D_lb x 2 D_lb x 1 nodes at
+    cell centres x_i = -1 + (i + 1/2)/D_lb (half-way walls lie on x, y = +-1).
+    Monopoles at (0, 0.1) and (0, -0.1), or rotated by 30 degrees at
+    (0.0839, 0.0866) and (0.1839, -0.0866); velocity in lattice units, the
+    physical field (rms 1) times U_lb; rho = 1."""
+    n = 2 * D_lb
+    i, j, _ = grid(n, n, 1)
+    x = -1.0 + (i + 0.5) / D_lb
+    y = -1.0 + (j + 0.5) / D_lb
+    (x1, y1), (x2, y2) = ((0.0839, 0.0866), (0.1839, -0.0866)) if inclined else ((0.0, 0.1), (0.0, -0.1))
+    e1 = np.exp(-((x - x1) ** 2 + (y - y1) ** 2) / r0 ** 2)
+    e2 = np.exp(-((x - x2) ** 2 + (y - y2) ** 2) / r0 ** 2)
+    a = 0.5 * abs(w_e)
+    ux = -a * (y - y1) * e1 + a * (y - y2) * e2
+    uy = a * (x - x1) * e1 - a * (x - x2) * e2
+    u = U_lb * np.stack([ux, uy, np.zeros_like(ux)])
+    return np.ones_like(ux), u
+
+
 def cavity_rest(n):
     return np.ones((n, n, n)), np.zeros((3, n, n, n))
 

@@ -69,3 +69,19 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert create(precision=9) == L.LBM_ERR_ARG
     assert L._lib.lbm_step(None, 1) == L.LBM_ERR_ARG
     assert L._lib.lbm_fields(None, None, None, None, None) == L.LBM_ERR_ARG
+
+
+def test_dipole_initial_energy_and_enstrophy():
+    """Sec. III.D states E(0) = 2 and Psi(0) = 800 for the dipole of w_e = 299.56,
+    r0 = 0.1 in [-1, 1]^2: the input recipe reproduces both (second-order
+    central differences, D_lb = 512)."""
+    import numpy as np
+    from paper_2010_01628_gb300 import inputs
+    D = 512
+    _, u = inputs.dipole(D, 1.0)
+    h = 1.0 / D
+    E = 0.5 * (u[0] ** 2 + u[1] ** 2).sum() * h * h
+    w = np.gradient(u[1, 0], h, axis=1) - np.gradient(u[0, 0], h, axis=0)
+    P = 0.5 * (w ** 2).sum() * h * h
+    assert abs(E - 2.0) < 1e-3
+    assert abs(P - 800.0) < 1.0
