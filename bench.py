@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2010_01628_gb300 import inputs  # noqa: E402
+from paper_2010_01628_gb300.ranks import Ranks, partition_domains  # noqa: E402
 
 METRIC = "D3Q19 CM-LBM MLUPS & % HBM roofline; time to 1e-6 residual, warm vs cold"
 N = 512
@@ -204,7 +205,8 @@ def run_reference(args):
     return 0
 
 
-def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=256, tune_cache="tmp", n_only=None):
+def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=256, tune_cache="tmp", n_only=None,
+                    ranks=None):
     """Throughput of the other configurations of the method, each with its own
     algorithmic bytes per lattice update (populations read + written plus the
     coupled fields).  ``only`` restricts the run to one of them (profiling)."""
@@ -222,7 +224,7 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
     if only in (None, "tg32"):
         out.update(_tg32(L, timed))
     if only in (None, "mhd_batch"):
-        out.update(_mhd_batch(L, timed, steps, peak, domains, tune_cache))
+        out.update(_mhd_batch(L, timed, steps, peak, domains, tune_cache, ranks))
     if only in (None, "cgm"):
         out.update(_cgm(L, timed, steps, peak, n_cgm))
     if only in (None, "sc"):
@@ -250,13 +252,17 @@ def _tg32(L, timed):
     return out
 
 
-def _mhd_batch(L, timed, steps, peak, domains, tune_cache="tmp"):
+def _mhd_batch(L, timed, steps, peak, domains, tune_cache="tmp", ranks=None):
     import tempfile
     out = {}
 
     # C3: Hartmann channels (64 by default), sizes {32,48,64,96}^3, Ha in [1,20], FP32 MHD,
-    # one persistent cooperative launch per call, captured in a CUDA graph.
-    sweep = inputs.hartmann_batch(domains, seed=2)
+    # one persistent cooperative launch per call, captured in a CUDA graph.  With several ranks the sweep's
+    # domains are partitioned by node count (no exchange between ranks): strong scaling of the fixed sweep.
+    full = inputs.hartmann_batch(domains, seed=2)
+    world = ranks.world if ranks else 1
+    mine = partition_domains([n ** 3 for n, _ in full], world)[ranks.rank if ranks else 0]
+    sweep = [full[i] for i in mine]
     nu = 0.1
     shapes = [(n, n, n) for n, _ in sweep]
     b0s = [2 * ha * nu / n for n, ha in sweep]
@@ -264,7 +270,7 @@ def _mhd_batch(L, timed, steps, peak, domains, tune_cache="tmp"):
                                precision="fp32", tau_m=0.5 + nu / 0.25,
                                g=[(8 * nu * 0.01 / n ** 2, 0.0, 0.0) for n, _ in sweep],
                                b_wall=[(0.0, b, 0.0) for b in b0s])
-    cells = sum(n ** 3 for n, _ in sweep)
+    cells = sum(n ** 3 for n, _ in full)
     for k, (n, _) in enumerate(sweep):
         r, uu, B = inputs.hartmann(n, b0s[k], nx=n, nz=n)
         L.lbm_init_fields(L.lbm_batch_domain(batch, k), r, uu, B=B)
@@ -272,14 +278,19 @@ def _mhd_batch(L, timed, steps, peak, domains, tune_cache="tmp"):
     tuned = L.lbm_autotune(batch, cache)  # no cache: every run times the candidates
     L.lbm_batch_step(batch, 4)
     n_b = max(20, steps)
+    if ranks:
+        ranks.barrier()
     t = timed(lambda n: L.lbm_batch_step(batch, n), n_b)
     L.lbm_sync(batch)
+    if ranks:
+        t = ranks.max_over_ranks(t)
     info = L.lbm_batch_info(batch)
     L.lbm_destroy(batch)
     ach = 320 * cells * n_b / t / 1e9
     out[f"mhd_batch_{domains}"] = {"MLUPS": cells * n_b / t / 1e6, "cells": cells, "steps": n_b, "bytes_per_lup": 320,
                            "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak, "launch": info,
-                           "autotune_MLUPS": tuned, "launches_per_call": 1}
+                           "autotune_MLUPS": tuned, "launches_per_call": 1, "ranks": world,
+                           "domains_on_rank0": len(mine)}
     return out
 
 
@@ -445,25 +456,18 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ranks = Ranks(device="cuda")
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2010_01628_gb300 import binding as L
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = ranks.max_over_ranks
 
     n, prec = args.n, args.precision
     stream = torch.cuda.current_stream()
@@ -475,7 +479,7 @@ def run_ours(args):
         peak, _ = measured_peaks()
         res = extra_workloads(L, torch, stream, args.steps, peak, only=args.only, domains=args.domains,
                               n_cgm=args.n, tune_cache=args.tune_cache,
-                              n_only=args.n if args.n != N else None)
+                              n_only=args.n if args.n != N else None, ranks=ranks)
         if rank == 0:
             print(json.dumps({"only": args.only, "workloads": res}), flush=True)
         return 0
@@ -547,7 +551,7 @@ def run_ours(args):
 
     extra = None
     if not args.no_variants:
-        extra = extra_workloads(L, torch, stream, args.steps, peak)
+        extra = extra_workloads(L, torch, stream, args.steps, peak, ranks=ranks)
         torch.cuda.empty_cache()
 
     cpu = None
