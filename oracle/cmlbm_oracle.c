@@ -906,8 +906,10 @@ static void cgm_gradient(const orc_params *p, const double *phi, int x, int y, i
 }
 
 /* App. E perturbation operator (Eq. eq:perturb) with the squared projection
- * (c_i . grad phi)^2, the form that conserves mass: added to the total
- * post-collision populations. */
+ * (c_i . grad phi)^2, the form that conserves mass.  Each colour k receives
+ * (A_k/2)|grad phi|[...]; with A_r = A_b = A both act on the total
+ * post-collision populations as A |grad phi| [...], the amplitude for which
+ * sigma = (2/9)(A_r + A_b)/omega = (4/9) A/omega (App. E). */
 void orc_cgm_perturb(const double *grad, double A, double *f)
 {
     double n2 = grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2];
@@ -917,7 +919,7 @@ void orc_cgm_perturb(const double *grad, double A, double *f)
         double cg = CX[i] * grad[0] + CY[i] * grad[1] + CZ[i] * grad[2];
         int c2 = CX[i] * CX[i] + CY[i] * CY[i] + CZ[i] * CZ[i];
         double Bi = c2 == 0 ? -1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
-        f[i] += 0.5 * A * nrm * (weight(i) * cg * cg / n2 - Bi);
+        f[i] += A * nrm * (weight(i) * cg * cg / n2 - Bi);
     }
 }
 

@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ 
     grad_phi<C>(phi, b, q, x, y, z, self, gr);
     const C n2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
     const C nrm = sqrt(n2);
-    const C pert_amp = (C)0.5 * (C)p.A * nrm;
+    // each colour's operator carries A_k/2 = A/2; together they perturb the total by A |grad phi| [...]
+    const C pert_amp = (C)p.A * nrm;
     const C inv_n2 = n2 > (C)1e-24 ? (C)1 / n2 : (C)0;
     const C inv_nrm = nrm > (C)1e-12 ? (C)1 / nrm : (C)0;
     const C inv_rho = recip(s.rho);

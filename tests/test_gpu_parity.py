@@ -350,3 +350,25 @@ def test_device_pointer_fields_roundtrip():
         L.lbm_destroy(ctx)
     np.testing.assert_array_equal(r_d.cpu().numpy(), host["rho"])
     np.testing.assert_array_equal(u_d.cpu().numpy(), host["u"])
+
+
+def test_cgm_sphere_laplace_law_fp32():
+    """App. E surface tension sigma = (4/9) A/omega: spheres of radius 12, 16, 20
+    in a 96^3 box (density ratio 1) carry dp = 2 sigma / R within 4 %."""
+    from paper_2010_01628_gb300 import binding as L
+    n, sigma, tau = 96, 5e-3, 1.0
+    ab = 1.0 / 3.0
+    for R in (12.0, 16.0, 20.0):
+        z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+        d = np.sqrt((x - (n - 1) / 2) ** 2 + (y - (n - 1) / 2) ** 2 + (z - (n - 1) / 2) ** 2)
+        ph = np.tanh((R - d) / 2.0)
+        ctx = L.lbm_create((n, n, n), 1 / tau, physics="cgm", precision="fp32", alpha_r=ab, alpha_b=ab,
+                           A=9 * sigma / tau / 4, beta=0.7)
+        try:
+            L.lbm_init_fields(ctx, np.ones_like(ph), np.zeros((3, n, n, n)), phase=ph)
+            L.lbm_step(ctx, 4000)
+            rho = L.lbm_fields(ctx, (n, n, n))["rho"]
+        finally:
+            L.lbm_destroy(ctx)
+        dp = (rho[n // 2, n // 2, n // 2] - rho[0, 0, 0]) * (1 - ab) / 2
+        assert abs(dp * R / (2 * sigma) - 1) < 0.04, (R, dp * R / (2 * sigma))
