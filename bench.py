@@ -206,7 +206,7 @@ def run_reference(args):
 
 
 def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=256, tune_cache="tmp", n_only=None,
-                    ranks=None):
+                    ranks=None, launch="auto"):
     """Throughput of the other configurations of the method, each with its own
     algorithmic bytes per lattice update (populations read + written plus the
     coupled fields).  ``only`` restricts the run to one of them (profiling)."""
@@ -228,7 +228,7 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
     if only in (None, "cgm"):
         out.update(_cgm(L, timed, steps, peak, n_cgm))
     if only in (None, "sc"):
-        out.update(_sc(L, timed, steps, peak, (n_only,) if n_only else (100, 256)))
+        out.update(_sc(L, timed, steps, peak, (n_only,) if n_only else (100, 256), launch))
     if only in (None, "rt"):
         out.update(_rt(L, timed, steps, peak))
     if only in (None, "appd"):
@@ -317,7 +317,7 @@ def _cgm(L, timed, steps, peak, n):
     return out
 
 
-def _sc(L, timed, steps, peak, sizes=(100, 256)):
+def _sc(L, timed, steps, peak, sizes=(100, 256), launch="auto"):
     out = {}
     # Shan-Chen static bubble (Sec. III.G): periodic n^3, nu = 0.0333, G = -5,
     # sharp 1.95 / 0.15 droplet, FP32: the paper's 100^3 with R = 20, and 256^3
@@ -329,6 +329,8 @@ def _sc(L, timed, steps, peak, sizes=(100, 256)):
         rho, u = inputs.static_bubble((n, n, n), R)
         c = L.lbm_create((n, n, n), 1 / (3 * 0.0333 + 0.5), physics="sc", precision="fp32", G=-5.0)
         L.lbm_init_fields(c, rho, u)
+        tuned = L.lbm_autotune(c, None) if launch == "auto" else apply_launch(L, c, launch, None)
+        shape = L.lbm_get_launch_shape(c)
         L.lbm_step(c, 3)
         n_c = max(20, steps // 2) * (8 if n == 100 else 1)
         t = timed(lambda k: L.lbm_step(c, k), n_c)
@@ -337,9 +339,11 @@ def _sc(L, timed, steps, peak, sizes=(100, 256)):
         ach = 160 * n ** 3 * n_c / t / 1e9
         out[f"sc_static_bubble_{n}"] = {
             "MLUPS": n ** 3 * n_c / t / 1e6, "steps": n_c, "radius": R, "bytes_per_lup": 160,
-            "moved_bytes_per_lup": 236, "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
-            "note": "two passes per step (pseudopotential, then collide with the interaction force); 160 B/LUP "
-                    "algorithmic (19 populations read and written, psi written and read once)"}
+            "moved_bytes_per_lup": 152 if shape["variant"] == "fused" else 236, "achieved_GBps": ach,
+            "frac_of_hbm_peak": ach / peak, "launch": shape, "autotune_MLUPS": tuned,
+            "note": "fused: one kernel per step, psi of three planes in shared memory; direct: two passes "
+                    "(pseudopotential, then collide); 160 B/LUP algorithmic (19 populations read and written, psi "
+                    "written and read once)"}
     return out
 
 
@@ -424,6 +428,8 @@ def apply_launch(L, ctx, spec, tune_cache):
         L.lbm_set_launch_shape(ctx, 0 if parts[0] == "direct" else 2, int(parts[1]) if len(parts) > 1 else 256, 0, 1)
     elif parts[0] == "tma":
         L.lbm_set_launch_shape(ctx, 1, 256, int(parts[1]), int(parts[2]))
+    elif parts[0] == "fused":
+        L.lbm_set_launch_shape(ctx, 3, int(parts[1]), int(parts[2]), 1)
     else:
         raise ValueError(spec)
     return None
@@ -479,7 +485,7 @@ def run_ours(args):
         peak, _ = measured_peaks()
         res = extra_workloads(L, torch, stream, args.steps, peak, only=args.only, domains=args.domains,
                               n_cgm=args.n, tune_cache=args.tune_cache,
-                              n_only=args.n if args.n != N else None, ranks=ranks)
+                              n_only=args.n if args.n != N else None, ranks=ranks, launch=args.launch)
         if rank == 0:
             print(json.dumps({"only": args.only, "workloads": res}), flush=True)
         return 0

@@ -238,7 +238,10 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int force, double 
  * TMA-staged kernel for single-phase flow (x-rows of 19 planes fetched into
  * shared memory by bulk copies, `stages` rows in flight per CTA, `ctas` CTAs
  * per SM); it needs nx * bytes-per-value to be a multiple of 16 and enough
- * shared memory for 2 stages, else LBM_ERR_UNSUPPORTED. */
+ * shared memory for 2 stages, else LBM_ERR_UNSUPPORTED; variant 3 = the fused
+ * Shan-Chen step (LBM_PHYS_SC only): CTAs of 32 x 8 (`threads` = 256) or
+ * 32 x 16 (512, FP32 only) threads march through `stages` z-planes each
+ * (0 = 32), keeping the pseudopotential of three planes in shared memory. */
 lbm_status lbm_set_launch_shape(lbm_ctx *ctx, int variant, int threads, int stages, int ctas);
 lbm_status lbm_get_launch_shape(const lbm_ctx *ctx, int *variant, int *threads, int *stages, int *ctas);
 

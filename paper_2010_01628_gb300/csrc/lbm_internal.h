@@ -41,6 +41,8 @@ struct lbm_ctx {
     int variant = 0;  // single-phase step: 0 = direct pulls, 1 = TMA-staged rows
     int tma_stages = 0;
     int tma_ctas = 1; // CTAs per SM of the TMA-staged kernel
+    int zchunk = 32;  // planes per CTA of the fused Shan-Chen kernel (variant 3)
+    int fused_threads = 256;  // threads per CTA of that kernel (32 x 8 or 32 x 16)
     int sms = 0;
     int* status = nullptr;  // device status word written by bounded waits
     std::string err;

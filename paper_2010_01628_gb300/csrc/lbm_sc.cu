@@ -87,7 +87,116 @@ __global__ void __launch_bounds__(256) sc_collide_kernel(const S* __restrict__ s
     scatter19<S, C>(dst, b.n, self, f);
 }
 
-// rho, u (with +F/2) and psi of a z-slab; psi of the whole box is current.
+// Fused step (launch variant 3): one kernel, psi kept on chip.  A CTA of
+// 32 x BY threads covers an x-y tile of 30 x (BY - 2) nodes plus a one-node
+// halo ring and marches through a chunk of lz planes.  For each plane z it
+// pulls plane z + 1 at every tile and halo node, writes that plane's psi into a
+// three-plane ring in shared memory, synchronises, and collides plane z at the
+// tile nodes with psi of all 18 neighbours read from the ring; the populations
+// of plane z + 1 stay in registers for the next plane.  psi never reaches HBM,
+// so a step reads and writes the populations once (160 B/LUP algorithmic at
+// FP32 becomes the traffic); the halo pulls are L2 hits of the neighbouring
+// tiles' rows, and each chunk pulls its two end planes once more.
+template <typename S, typename C, bool WALLS, int BY>
+__global__ void __launch_bounds__(32 * BY) sc_fused_kernel(const S* __restrict__ src, S* __restrict__ dst, ScArgs p,
+                                                           int lz) {
+    constexpr int BX = 32, TX = BX - 2, TY = BY - 2;
+    __shared__ C ring[3][BY][BX];
+    const Box& b = p.box;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int gx = (int)blockIdx.x * TX + tx - 1, gy = (int)blockIdx.y * TY + ty - 1;
+    const int z0 = (int)blockIdx.z * lz, z1 = min(z0 + lz, b.nz);
+    const bool px = b.periodic & 1u, py = b.periodic & 2u, pz = b.periodic & 4u;
+    // this thread's node (wrapped on periodic axes; absent beyond a wall)
+    int wx = gx, wy = gy;
+    bool inside = true;
+    if (gx < 0 || gx >= b.nx) {
+        if (px)
+            wx = ((gx % b.nx) + b.nx) % b.nx;
+        else
+            inside = false;
+    }
+    if (gy < 0 || gy >= b.ny) {
+        if (py)
+            wy = ((gy % b.ny) + b.ny) % b.ny;
+        else
+            inside = false;
+    }
+    const bool interior = tx >= 1 && tx <= TX && ty >= 1 && ty <= TY && gx < b.nx && gy < b.ny;
+    const C lx = (C)p.lid[0], ly = (C)p.lid[1], lzv = (C)p.lid[2];
+    auto pull = [&](int zz, C (&f)[Q]) {
+        const Nbr q = make_nbr(b, wx, wy, zz);
+        const uint32_t self = ((uint32_t)zz * (uint32_t)b.ny + (uint32_t)wy) * (uint32_t)b.nx + (uint32_t)wx;
+        gather19<S, C, WALLS>(src, b, q, wx, wy, zz, self, lx, ly, lzv, f);
+    };
+    auto slot = [&](int zz) { return (zz - z0 + 1) % 3; };
+
+    C f[Q];
+    {
+        const int zm = z0 - 1;
+        if (inside && (zm >= 0 || pz)) {
+            C t[Q];
+            pull(zm >= 0 ? zm : zm + b.nz, t);
+            ring[slot(zm)][ty][tx] = pseudopotential<C>((C)1 + moments19(t).drho);
+        }
+        if (inside) {
+            pull(z0, f);
+            ring[slot(z0)][ty][tx] = pseudopotential<C>((C)1 + moments19(f).drho);
+        }
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int zn = z + 1;
+        C fn[Q];
+        const bool next = inside && (zn < b.nz || pz);
+        if (next) {
+            pull(zn < b.nz ? zn : zn - b.nz, fn);
+            ring[slot(zn)][ty][tx] = pseudopotential<C>((C)1 + moments19(fn).drho);
+        }
+        __syncthreads();
+        if (interior) {
+            const Nbr q = make_nbr(b, gx, gy, z);
+            const int sm = slot(z - 1), s0 = slot(z), sp = slot(zn);
+            const C own = ring[s0][ty][tx];
+            C sx = (C)0, sy = (C)0, sz = (C)0;
+#define LBM_SCF(I)                                                                                          \
+    {                                                                                                       \
+        constexpr int ex = cx_of(I), ey = cy_of(I), ez = cz_of(I);                                          \
+        const bool wall = WALLS && ((ex > 0 && q.wxp) || (ex < 0 && q.wxm) || (ey > 0 && q.wyp) ||          \
+                                    (ey < 0 && q.wym) || (ez > 0 && q.wzp) || (ez < 0 && q.wzm));           \
+        const C t = (wall ? own : ring[ez == 0 ? s0 : (ez > 0 ? sp : sm)][ty + ey][tx + ex]) * (C)w_of(I);  \
+        if (ex) sx += (C)ex * t;                                                                            \
+        if (ey) sy += (C)ey * t;                                                                            \
+        if (ez) sz += (C)ez * t;                                                                            \
+    }
+            LBM_SCF(1) LBM_SCF(2) LBM_SCF(3) LBM_SCF(4) LBM_SCF(5) LBM_SCF(6) LBM_SCF(7) LBM_SCF(8) LBM_SCF(9)
+            LBM_SCF(10) LBM_SCF(11) LBM_SCF(12) LBM_SCF(13) LBM_SCF(14) LBM_SCF(15) LBM_SCF(16) LBM_SCF(17)
+            LBM_SCF(18)
+#undef LBM_SCF
+            const Moments<C> m = moments19(f);
+            Macro<C> a;
+            a.rho = (C)1 + m.drho;
+            const C mg = -(C)p.G * own;
+            a.Fx = (a.rho * (C)p.g[0] - (C)p.rg[0]) + mg * sx;
+            a.Fy = (a.rho * (C)p.g[1] - (C)p.rg[1]) + mg * sy;
+            a.Fz = (a.rho * (C)p.g[2] - (C)p.rg[2]) + mg * sz;
+            const C inv = recip(a.rho);
+            a.ux = (m.jx + (C)0.5 * a.Fx) * inv;
+            a.uy = (m.jy + (C)0.5 * a.Fy) * inv;
+            a.uz = (m.jz + (C)0.5 * a.Fz) * inv;
+            collide_fluid<C>(f, m, a, (C)p.omega);
+            conserve_mass<C>(f, m.drho);
+            const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)gy) * (uint32_t)b.nx + (uint32_t)gx;
+            scatter19<S, C>(dst, b.n, self, f);
+        }
+        __syncthreads();
+        if (next) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = fn[i];
+        }
+    }
+}
+
+// rho, u (with +F/2) and psi of a z-slab; psi of the whole box is current.// rho, u (with +F/2) and psi of a z-slab; psi of the whole box is current.
 template <typename S, typename C, bool WALLS>
 __global__ void sc_fields_kernel(const S* __restrict__ src, const C* __restrict__ psi, double* __restrict__ slab,
                                  ScArgs p, int z0, int nzs) {
@@ -161,11 +270,32 @@ static void launch_psi(lbm_ctx* c, const S* src, const ScArgs& p) {
         sc_psi_kernel<S, C, false><<<grid, c->block_x, 0, c->stream>>>(src, (C*)c->phi, p);
 }
 
+template <typename S, typename C, bool WALLS, int BY>
+static void launch_fused(lbm_ctx* c, const S* src, S* dst, const ScArgs& p) {
+    const int lz = c->zchunk > 0 ? c->zchunk : 32;
+    const dim3 grid((unsigned)((c->box.nx + 29) / 30), (unsigned)((c->box.ny + BY - 3) / (BY - 2)),
+                    (unsigned)((c->box.nz + lz - 1) / lz));
+    sc_fused_kernel<S, C, WALLS, BY><<<grid, dim3(32, BY), 0, c->stream>>>(src, dst, p, lz);
+}
+
 template <typename S, typename C>
 static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const ScArgs p = sc_args(c);
     const bool walls = (c->box.periodic & 7u) != 7u;
     const int bx = c->block_x;
+    if (c->variant == 3) {
+        const bool wide = c->fused_threads >= 512 && sizeof(C) == 4;
+        for (long s = 0; s < n; ++s) {
+            const S* src = (const S*)c->buf[c->cur];
+            S* dst = (S*)c->buf[c->cur ^ 1];
+            if (walls)
+                wide ? launch_fused<S, C, true, 16>(c, src, dst, p) : launch_fused<S, C, true, 8>(c, src, dst, p);
+            else
+                wide ? launch_fused<S, C, false, 16>(c, src, dst, p) : launch_fused<S, C, false, 8>(c, src, dst, p);
+            if (!dry) c->cur ^= 1;
+        }
+        return cudaGetLastError();
+    }
     const dim3 grid = step_grid(c->box, bx);
     const C* psi = (const C*)c->phi;
     for (long s = 0; s < n; ++s) {

@@ -157,6 +157,15 @@ float time_dry_steps(lbm_ctx* c, long reps, cudaError_t* err) {
 
 extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads, int stages, int ctas) {
     if (!c || c->batch || !c->owns) return LBM_ERR_ARG;
+    if (variant == 3) {  // fused Shan-Chen step: 32 x 8 or 32 x 16 threads, `stages` planes per CTA
+        if (c->physics != LBM_PHYS_SC) return LBM_ERR_UNSUPPORTED;
+        if ((threads != 256 && threads != 512) || stages < 0 || stages > 4096) return LBM_ERR_ARG;
+        if (threads == 512 && c->prec == LBM_FP64) return LBM_ERR_UNSUPPORTED;
+        c->variant = 3;
+        c->fused_threads = threads;
+        c->zchunk = stages > 0 ? stages : 32;
+        return LBM_OK;
+    }
     if (threads < 32 || threads > 256 || threads % 32 != 0) return LBM_ERR_ARG;
     if (variant == 0 || variant == 2) {
         if (variant == 2 && !(c->physics == LBM_PHYS_FLUID &&
@@ -181,8 +190,8 @@ extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads,
 extern "C" lbm_status lbm_get_launch_shape(const lbm_ctx* c, int* variant, int* threads, int* stages, int* ctas) {
     if (!c || c->batch) return LBM_ERR_ARG;
     if (variant) *variant = c->variant;
-    if (threads) *threads = c->block_x;
-    if (stages) *stages = c->variant == 1 ? c->tma_stages : 0;
+    if (threads) *threads = c->variant == 3 ? c->fused_threads : c->block_x;
+    if (stages) *stages = c->variant == 1 ? c->tma_stages : (c->variant == 3 ? c->zchunk : 0);
     if (ctas) *ctas = c->variant == 1 ? c->tma_ctas : 0;
     return LBM_OK;
 }
@@ -214,10 +223,17 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
             const int cps = h.count("ctas_per_sm") ? (int)h["ctas_per_sm"] : 0;
             if (lbm::batch_apply_config(c, threads, cps) != cudaSuccess) return LBM_ERR_CUDA;
         } else {
-            c->block_x = threads;
             const int variant = h.count("variant") ? (int)h["variant"] : 0;
             const int stages = h.count("stages") ? (int)h["stages"] : 0;
             const int ctas = h.count("ctas") ? (int)h["ctas"] : 1;
+            if (variant == 3 && c->physics == LBM_PHYS_SC) {
+                c->variant = 3;
+                c->fused_threads = threads;
+                c->zchunk = stages > 0 ? stages : 32;
+                if (mlups) *mlups = h.count("mlups") ? h["mlups"] : 0.0;
+                return LBM_OK;
+            }
+            c->block_x = threads;
             if (variant == 1 && stages >= 2 && stages <= lbm::fluid_tma_max_stages(c, ctas)) {
                 c->variant = 1;
                 c->tma_stages = stages;
@@ -268,11 +284,21 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
             for (int st : {2, 3, 4, 6, 8})
                 if (st <= smax) cands.push_back({1, c->block_x, st, ctas});
         }
+        if (c->physics == LBM_PHYS_SC)
+            for (int th : {256, 512})
+                for (int lz : {16, 32, 64})
+                    if (th == 256 || c->prec != LBM_FP64) cands.push_back({3, th, lz, 1});
         const int saved_bx = c->block_x, saved_var = c->variant, saved_st = c->tma_stages, saved_ct = c->tma_ctas;
+        const int saved_ft = c->fused_threads, saved_lz = c->zchunk;
         for (const Cand& k : cands) {
             c->variant = k.variant;
-            c->block_x = k.threads;
-            c->tma_stages = k.stages > 0 ? k.stages : saved_st;
+            if (k.variant == 3) {
+                c->fused_threads = k.threads;
+                c->zchunk = k.stages;
+            } else {
+                c->block_x = k.threads;
+            }
+            c->tma_stages = k.variant == 1 && k.stages > 0 ? k.stages : saved_st;
             c->tma_ctas = k.ctas;
             float one = time_dry_steps(c, 1, &e);  // warm-up and size estimate
             if (e != cudaSuccess) {
@@ -296,15 +322,22 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
                              {"ctas", (double)k.ctas}};
             }
         }
+        c->block_x = saved_bx;
+        c->fused_threads = saved_ft;
+        c->zchunk = saved_lz;
         if (best.empty()) {
-            c->block_x = saved_bx;
             c->variant = saved_var;
             c->tma_stages = saved_st;
             c->tma_ctas = saved_ct;
             return LBM_ERR_CUDA;
         }
-        c->block_x = (int)best["threads"];
         c->variant = (int)best["variant"];
+        if (c->variant == 3) {
+            c->fused_threads = (int)best["threads"];
+            c->zchunk = (int)best["stages"];
+        } else {
+            c->block_x = (int)best["threads"];
+        }
         if (c->variant == 1) {
             c->tma_stages = (int)best["stages"];
             c->tma_ctas = (int)best["ctas"];

@@ -13,7 +13,11 @@ pytestmark = pytest.mark.gpu
 G = -5.0
 NU = 0.0333
 OMEGA = 1.0 / (3.0 * NU + 0.5)
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+# FP32: both phases sit at O(1) density deviations, where FP32 arithmetic
+# rounds at eps32 * rho per population and step.  The FP64 oracle perturbed by
+# noise of that size moves u by 0.85e-5 to 1.15e-5 on these cases (three seeds
+# each), and the GPU lands on the same values; the bound is twice that.
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
 FIELDS = ("rho", "u", "phase")
 
 
@@ -166,3 +170,43 @@ def test_laplace_law_paper_configuration_fp32():
     B = np.vstack([1.0 / radii, 1.0 / radii ** 2]).T
     (two_sigma, b), *_ = np.linalg.lstsq(B, dp, rcond=None)
     assert two_sigma > 0 and np.abs((dp - B @ np.array([two_sigma, b])) / dp).max() <= 0.01, (dp, two_sigma, b)
+
+
+@pytest.mark.parametrize("precision,threads,lz", [("fp64", 256, 7), ("fp32", 256, 16), ("fp32", 512, 32)])
+@pytest.mark.parametrize("shape,periodic", [((40, 36, 34), (True, True, True)), ((13, 11, 9), (False, False, False)),
+                                            ((70, 5, 6), (True, False, True)), ((1, 30, 20), (True, True, True))])
+def test_fused_kernel_against_oracle(precision, threads, lz, shape, periodic):
+    """The fused step (psi in a shared-memory ring, z-chunks of lz planes with
+    ragged last chunks and tiles) against the oracle: periodic, all walls with a
+    lid and gravity, mixed, and a one-node-thick slab."""
+    rho, u = inputs.static_bubble(shape, min(shape[1:]) / 4.0, width=1.5, noise=1e-3, seed=13)
+    # gravity only where a wall carries it (in a periodic box it accelerates the whole box)
+    g = (0.0, 0.0, 0.0) if periodic[1] else (0.0, -5e-5, 0.0)
+    kw = dict(periodic=periodic, G=G, g=g, lid_u=(0.02, 0.0, 0.0))
+    o = oracle_run(shape, OMEGA, 25, rho, u, physics="sc", **kw)
+    r = gpu_run(shape, OMEGA, 25, rho, u, physics="sc", precision=precision, launch=(3, threads, lz, 1), **kw)
+    compare(r, o, TOL[precision])
+
+
+def test_fused_and_two_pass_agree_fp64():
+    from paper_2010_01628_gb300 import binding as L
+    shape = (40, 36, 34)
+    rho, u = inputs.static_bubble(shape, 9.0, noise=1e-3, seed=5)
+    out = []
+    for launch in ((0, 64, 0, 1), (3, 256, 32, 1)):
+        r = gpu_run(shape, OMEGA, 40, rho, u, physics="sc", G=G, precision="fp64", launch=launch)
+        out.append(r)
+    for k in ("rho", "u", "phase"):
+        np.testing.assert_allclose(out[0][k], out[1][k], rtol=0, atol=1e-14)
+
+
+def test_fused_and_two_pass_agree_fp32():
+    """FP32: the fused step reproduces the two-pass step on the same case (the
+    two paths take the same psi, force sum and collision in the same order)."""
+    shape = (40, 36, 34)
+    rho, u = inputs.static_bubble(shape, 8.5, width=1.5, noise=1e-3, seed=13)
+    out = [gpu_run(shape, OMEGA, 25, rho, u, physics="sc", G=G, precision="fp32", launch=launch)
+           for launch in ((0, 64, 0, 1), (3, 256, 16, 1), (3, 512, 32, 1))]
+    for other in out[1:]:
+        for k in ("rho", "u", "phase"):
+            assert rel_l2(other[k], out[0][k]) < 1e-6, k
