@@ -140,8 +140,11 @@ __global__ void __launch_bounds__(32 * BY) sc_fused_kernel(const S* __restrict__
             ring[slot(zm)][ty][tx] = pseudopotential<C>((C)1 + moments19(t).drho);
         }
         if (inside) {
-            pull(z0, f);
-            ring[slot(z0)][ty][tx] = pseudopotential<C>((C)1 + moments19(f).drho);
+            C t[Q];
+            pull(z0, t);
+            ring[slot(z0)][ty][tx] = pseudopotential<C>((C)1 + moments19(t).drho);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = t[i];
         }
     }
     for (int z = z0; z < z1; ++z) {
