@@ -26,12 +26,16 @@ def run_uniform_acceleration(shape, precision, g, steps):
     return mass, mom
 
 
-@pytest.mark.parametrize("shape,precision,tol", [((2047, 1024, 1024), "bf16", 1e-2), ((1024, 1024, 1024), "fp32", 1e-5)])
-def test_largest_domains_uniform_acceleration(shape, precision, tol):
+# mass: every node holds the same state, so storage rounding is coherent; one
+# rounding of the stored (f - w)/w moves rho by at most eps * Sum_i w_i |q_i|,
+# about 2^-8 u ~ 4e-6 for BF16 at u ~ 1e-3 (measured 2.1e-6), 1e-9 for FP32.
+@pytest.mark.parametrize("shape,precision,tol,tol_mass", [((2047, 1024, 1024), "bf16", 1e-2, 1e-5),
+                                                          ((1024, 1024, 1024), "fp32", 1e-5, 1e-6)])
+def test_largest_domains_uniform_acceleration(shape, precision, tol, tol_mass):
     n = shape[0] * shape[1] * shape[2]
     g, steps = 1e-4, 10
     mass, mom = run_uniform_acceleration(shape, precision, g, steps)
-    assert abs(mass / n - 1.0) < 1e-6
+    assert abs(mass / n - 1.0) < tol_mass
     assert abs(mom[0] / (n * (steps + 0.5) * g) - 1.0) < tol
     assert abs(mom[1]) < 1e-9 * n and abs(mom[2]) < 1e-9 * n
 
