@@ -418,14 +418,16 @@ def _channel(L, timed, steps, peak, n=512):
 
 
 def apply_launch(L, ctx, spec, tune_cache):
-    """'auto': autotune (timed dry runs, state unchanged); 'direct[:threads]' or
-    'tma:stages:ctas': a fixed launch shape (profiling).  Returns the tuned
+    """'auto': autotune (timed dry runs, state unchanged); 'direct[:threads]',
+    'pair[:threads]', 'zpair[:threads]', 'fused:threads:planes' or 'tma:stages:ctas': a
+    fixed launch shape (profiling).  Returns the tuned
     MLUPS or None."""
     if spec == "auto":
         return L.lbm_autotune(ctx, tune_cache)
     parts = spec.split(":")
-    if parts[0] in ("direct", "pair"):
-        L.lbm_set_launch_shape(ctx, 0 if parts[0] == "direct" else 2, int(parts[1]) if len(parts) > 1 else 256, 0, 1)
+    if parts[0] in ("direct", "pair", "zpair"):
+        L.lbm_set_launch_shape(ctx, {"direct": 0, "pair": 2, "zpair": 4}[parts[0]],
+                               int(parts[1]) if len(parts) > 1 else 256, 0, 1)
     elif parts[0] == "tma":
         L.lbm_set_launch_shape(ctx, 1, 256, int(parts[1]), int(parts[2]))
     elif parts[0] == "fused":
@@ -600,7 +602,7 @@ def main():
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     ap.add_argument("--launch", default="auto",
                     help="launch shape of the single-phase step: auto | direct[:threads] | pair[:threads] | "
-                         "tma:stages:ctas")
+                         "zpair[:threads] | tma:stages:ctas | fused:threads:planes")
     ap.add_argument("--tune-cache", default="tmp", choices=["tmp", "none"],
                     help="autotuner cache of the batch workload: a file in the temp dir, or none")
     args = ap.parse_args()

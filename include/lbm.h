@@ -234,7 +234,10 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int force, double 
  * chooses): variant 0 = one thread per node pulling straight from global
  * memory (`threads` per block: 32..256, multiple of 32); variant 2 = two
  * x-neighbour nodes per thread with aligned 32-bit accesses (16-bit storage,
- * even nx, single phase); variant 1 = the
+ * even nx, single phase); variant 4 = two z-neighbour nodes per thread with
+ * plain 2-byte pulls (16-bit storage, single phase); variants 2 and 4 relax
+ * both nodes with packed FP32x2 arithmetic (same rounding per node as the
+ * scalar FP32 code, different fma contraction); variant 1 = the
  * TMA-staged kernel for single-phase flow (x-rows of 19 planes fetched into
  * shared memory by bulk copies, `stages` rows in flight per CTA, `ctas` CTAs
  * per SM); it needs nx * bytes-per-value to be a multiple of 16 and enough

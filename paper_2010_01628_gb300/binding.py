@@ -393,7 +393,7 @@ _lib.lbm_get_launch_shape.restype = ctypes.c_int
 def lbm_get_launch_shape(ctx):
     v = [ctypes.c_int() for _ in range(4)]
     _check(_lib.lbm_get_launch_shape(ctx, *[ctypes.byref(x) for x in v]), ctx)
-    return {"variant": ["direct", "tma", "pair", "fused"][v[0].value], "threads": v[1].value, "stages": v[2].value,
+    return {"variant": ["direct", "tma", "pair", "fused", "zpair"][v[0].value], "threads": v[1].value, "stages": v[2].value,
             "ctas_per_sm": v[3].value}
 
 

@@ -396,6 +396,7 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
         if (physics == LBM_PHYS_MHD) {
             D.mh.tau_m = phys[d].tau_m;
             D.mh.inv_tau_m = 1.0 / phys[d].tau_m;
+            D.mh.jfac = 1.0 / (phys[d].tau_m * lbm::CSM2);
             for (int a = 0; a < 3; ++a) {
                 D.mh.g[a] = D.fl.g[a];
                 D.mh.bw[a] = phys[d].b_wall[a];

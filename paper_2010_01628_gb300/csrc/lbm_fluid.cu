@@ -8,6 +8,7 @@
 // moment to its forced equilibrium value, rebuild f* with the two-step
 // transform of App. C and store it, coalesced, to the other buffer.
 #include "lbm_fluid.cuh"
+#include "lbm_pack2.cuh"
 #include "lbm_internal.h"
 #include "lbm_reduce.cuh"
 
@@ -70,17 +71,19 @@ template <>
 struct Pair16<__half> {
     __device__ static __forceinline__ float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
     __device__ static __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-    __device__ static __forceinline__ uint32_t pack(float a, float b) {
-        return (uint32_t)__half_as_ushort(__float2half_rn(a)) | ((uint32_t)__half_as_ushort(__float2half_rn(b)) << 16);
+    // one conversion instruction rounds and packs both lanes (x low, y high)
+    __device__ static __forceinline__ uint32_t pack(float2 v) {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        return *reinterpret_cast<const uint32_t*>(&h);
     }
 };
 template <>
 struct Pair16<__nv_bfloat16> {
     __device__ static __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
     __device__ static __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-    __device__ static __forceinline__ uint32_t pack(float a, float b) {
-        return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
-               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+    __device__ static __forceinline__ uint32_t pack(float2 v) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        return *reinterpret_cast<const uint32_t*>(&h);
     }
 };
 
@@ -95,9 +98,8 @@ struct PairCtx {
 // with half-way bounce-back replacements.  Every lane of the warp executes the
 // shuffles (inactive lanes past the row end carry zeros).
 template <typename S, bool WALLS, int I>
-__device__ __forceinline__ void gather_pair(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
-                                            const PairCtx& t, int y, int z, float lx, float ly, float lz, float& fa,
-                                            float& fb) {
+__device__ __forceinline__ P2 gather_pair(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
+                                          const PairCtx& t, int y, int z, float lx, float ly, float lz) {
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
     constexpr float w = (float)w_of(I);
     const int sy = cy == 0 ? y : (cy > 0 ? q.ym : q.yp);
@@ -118,8 +120,7 @@ __device__ __forceinline__ void gather_pair(const uint32_t* __restrict__ src, co
         if (t.lane == 31 || t.x0 + 2 >= b.nx) nv = ld ? __ldg(P + row_w + (t.x0 + 2 >= b.nx ? 0u : own + 1)) : 0u;
         val = __byte_perm(wv, nv, 0x5432);
     }
-    fa = Pair16<S>::lo(val) * w;
-    fb = Pair16<S>::hi(val) * w;
+    P2 f = P2(Pair16<S>::lo(val), Pair16<S>::hi(val)) * P2(w);
     if (WALLS) {
         // half-way bounce-back: the node's own post-collision population of the
         // opposite direction (+ the moving-lid term when the +y face is crossed)
@@ -129,10 +130,11 @@ __device__ __forceinline__ void gather_pair(const uint32_t* __restrict__ src, co
             const uint32_t ov = t.active ? __ldg(src + (size_t)opp_of(I) * t.plane_w + t.self_w) : 0u;
             const float lid = (cy < 0 && q.wyp) ? (float)(6.0 * w_of(I)) * ((float)cx * lx + (float)cy * ly + (float)cz * lz)
                                                 : 0.f;
-            if (wall_a) fa = Pair16<S>::lo(ov) * w + lid;
-            if (wall_b) fb = Pair16<S>::hi(ov) * w + lid;
+            if (wall_a) f.v.x = Pair16<S>::lo(ov) * w + lid;
+            if (wall_b) f.v.y = Pair16<S>::hi(ov) * w + lid;
         }
     }
+    return f;
 }
 
 template <typename S, bool WALLS>
@@ -152,27 +154,73 @@ __global__ void __launch_bounds__(256) fluid_step_pair_kernel(const S* __restric
     // of cell x0+1 is tested in gather_pair
     const Nbr q = make_nbr(b, t.active ? t.x0 : 0, y, z);
     const float lx = (float)p.lid[0], ly = (float)p.lid[1], lz = (float)p.lid[2];
-    float fa[Q], fb[Q];
-#define LBM_GP(I) gather_pair<S, WALLS, I>(src, b, q, t, y, z, lx, ly, lz, fa[I], fb[I]);
+    P2 f[Q];
+#define LBM_GP(I) f[I] = gather_pair<S, WALLS, I>(src, b, q, t, y, z, lx, ly, lz);
     LBM_GP(0) LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9)
     LBM_GP(10) LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
 #undef LBM_GP
     if (!t.active) return;
-    {
-        const Moments<float> m = moments19(fa);
-        const Macro<float> a = fluid_macro(m, (float)p.g[0], (float)p.g[1], (float)p.g[2]);
-        collide_fluid<float>(fa, m, a, (float)p.omega);
-    }
-    {
-        const Moments<float> m = moments19(fb);
-        const Macro<float> a = fluid_macro(m, (float)p.g[0], (float)p.g[1], (float)p.g[2]);
-        collide_fluid<float>(fb, m, a, (float)p.omega);
-    }
+    // both cells through one packed collision
+    const Moments<P2> m = moments19(f);
+    const Macro<P2> a = fluid_macro(m, P2((float)p.g[0]), P2((float)p.g[1]), P2((float)p.g[2]));
+    collide_fluid<P2>(f, m, a, P2((float)p.omega));
 #define LBM_SP(I) \
-    __stcs(dst + (size_t)I * t.plane_w + t.self_w, Pair16<S>::pack(fa[I] * (float)(1.0 / w_of(I)), fb[I] * (float)(1.0 / w_of(I))));
+    __stcs(dst + (size_t)I * t.plane_w + t.self_w, Pair16<S>::pack(P2(f[I] * P2((float)(1.0 / w_of(I)))).v));
     LBM_SP(0) LBM_SP(1) LBM_SP(2) LBM_SP(3) LBM_SP(4) LBM_SP(5) LBM_SP(6) LBM_SP(7) LBM_SP(8) LBM_SP(9)
     LBM_SP(10) LBM_SP(11) LBM_SP(12) LBM_SP(13) LBM_SP(14) LBM_SP(15) LBM_SP(16) LBM_SP(17) LBM_SP(18)
 #undef LBM_SP
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit storage, two nodes per thread stacked in z: (x, y, z0) and
+// (x, y, z0 + 1), z0 even (for odd nz the last thread updates z0 alone).  Every
+// pull is a plain 2-byte load of the stored q = (f - w)/w; one packed multiply
+// per direction scales both nodes to f - w, one packed collision relaxes both,
+// and one packed multiply scales back before the two stores.
+template <typename S, bool WALLS, int I>
+__device__ __forceinline__ float pull_q(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
+                                        uint32_t self, float lx, float ly, float lz) {
+    uint32_t cell;
+    const bool wall = pull_source<I>(b, q, x, y, z, cell);
+    if (!WALLS || !wall) return Store<S>::load(src + (size_t)I * b.n + cell);
+    // half-way bounce-back; the lid term 6 w c.u_lid is 6 c.u_lid in units of w
+    float v = Store<S>::load(src + (size_t)opp_of(I) * b.n + self);
+    if (cy_of(I) < 0 && q.wyp) v += 6.f * ((float)cx_of(I) * lx + (float)cy_of(I) * ly + (float)cz_of(I) * lz);
+    return v;
+}
+
+template <typename S, bool WALLS>
+__global__ void __launch_bounds__(256) fluid_step_zpair_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                               FluidArgs p) {
+    const Box& b = p.box;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= b.nx) return;
+    const int y = blockIdx.y, za = 2 * (int)blockIdx.z;
+    const bool two = za + 1 < b.nz;
+    const int zb = two ? za + 1 : za;
+    const uint32_t sa = ((uint32_t)za * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    const uint32_t sb = ((uint32_t)zb * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
+    const Nbr qa = make_nbr(b, x, y, za), qb = make_nbr(b, x, y, zb);
+    const float lx = (float)p.lid[0], ly = (float)p.lid[1], lz = (float)p.lid[2];
+    P2 f[Q];
+#define LBM_ZP(I)                                                                                 \
+    f[I] = P2(pull_q<S, WALLS, I>(src, b, qa, x, y, za, sa, lx, ly, lz),                          \
+              pull_q<S, WALLS, I>(src, b, qb, x, y, zb, sb, lx, ly, lz)) * P2((float)w_of(I));
+    LBM_ZP(0) LBM_ZP(1) LBM_ZP(2) LBM_ZP(3) LBM_ZP(4) LBM_ZP(5) LBM_ZP(6) LBM_ZP(7) LBM_ZP(8) LBM_ZP(9)
+    LBM_ZP(10) LBM_ZP(11) LBM_ZP(12) LBM_ZP(13) LBM_ZP(14) LBM_ZP(15) LBM_ZP(16) LBM_ZP(17) LBM_ZP(18)
+#undef LBM_ZP
+    const Moments<P2> m = moments19(f);
+    const Macro<P2> a = fluid_macro(m, P2((float)p.g[0]), P2((float)p.g[1]), P2((float)p.g[2]));
+    collide_fluid<P2>(f, m, a, P2((float)p.omega));
+#define LBM_ZS(I)                                                      \
+    {                                                                  \
+        const P2 o = f[I] * P2((float)(1.0 / w_of(I)));                \
+        Store<S>::store(dst + (size_t)I * b.n + sa, o.v.x);            \
+        if (two) Store<S>::store(dst + (size_t)I * b.n + sb, o.v.y);   \
+    }
+    LBM_ZS(0) LBM_ZS(1) LBM_ZS(2) LBM_ZS(3) LBM_ZS(4) LBM_ZS(5) LBM_ZS(6) LBM_ZS(7) LBM_ZS(8) LBM_ZS(9)
+    LBM_ZS(10) LBM_ZS(11) LBM_ZS(12) LBM_ZS(13) LBM_ZS(14) LBM_ZS(15) LBM_ZS(16) LBM_ZS(17) LBM_ZS(18)
+#undef LBM_ZS
 }
 
 // ---------------------------------------------------------------------------
@@ -491,11 +539,21 @@ static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     }
     const dim3 grid = step_grid(c->box, bx);
     const bool pair = is16<S>() && c->variant == 2 && (c->box.nx % 2 == 0);
+    const bool zpair = is16<S>() && c->variant == 4;
     const dim3 grid2((unsigned)((c->box.nx / 2 + bx - 1) / bx), (unsigned)c->box.ny, (unsigned)c->box.nz);
+    const dim3 gridz(grid.x, grid.y, (unsigned)((c->box.nz + 1) / 2));
     for (long s = 0; s < n; ++s) {
         const S* src = (const S*)c->buf[c->cur];
         S* dst = (S*)c->buf[c->cur ^ 1];
         if constexpr (is16<S>()) {
+            if (zpair) {
+                if (walls)
+                    fluid_step_zpair_kernel<S, true><<<gridz, bx, 0, c->stream>>>(src, dst, p);
+                else
+                    fluid_step_zpair_kernel<S, false><<<gridz, bx, 0, c->stream>>>(src, dst, p);
+                if (!dry) c->cur ^= 1;
+                continue;
+            }
             if (pair) {
                 if (walls)
                     fluid_step_pair_kernel<S, true><<<grid2, bx, 0, c->stream>>>(src, dst, p);

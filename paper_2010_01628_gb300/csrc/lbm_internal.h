@@ -38,7 +38,7 @@ struct lbm_ctx {
     lbm_free_fn release;
     void* user;
     int block_x;      // threads per block along x for the step kernels
-    int variant = 0;  // single-phase step: 0 = direct pulls, 1 = TMA-staged rows
+    int variant = 0;  // 0 direct pulls, 1 TMA-staged rows, 2 16-bit x-pairs, 3 fused Shan-Chen, 4 16-bit z-pairs
     int tma_stages = 0;
     int tma_ctas = 1; // CTAs per SM of the TMA-staged kernel
     int zchunk = 32;  // planes per CTA of the fused Shan-Chen kernel (variant 3)
@@ -78,6 +78,12 @@ cudaError_t fluid_step(lbm_ctx* c, long n, bool dry = false);
 // Largest stage count of the TMA-staged kernel that fits `ctas` CTAs per SM (0
 // if the geometry does not allow the variant).
 int fluid_tma_max_stages(const lbm_ctx* c, int ctas);
+// The 16-bit single-phase step with two nodes per thread and packed FP32x2
+// arithmetic (launch variants 2 and 4): D3Q19 central moments, bounce-back walls.
+inline bool packed16_ok(const lbm_ctx* c) {
+    return c->physics == LBM_PHYS_FLUID && (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) &&
+           c->grid.wall_model == LBM_WALL_BOUNCE_BACK && c->relax.moment_space == LBM_MOMENTS_CENTRAL && c->q == 19;
+}
 cudaError_t fluid_init(lbm_ctx* c, const double* slab, int z0, int nzs, bool uniform);
 cudaError_t fluid_fields(lbm_ctx* c, double* slab, int z0, int nzs);
 cudaError_t fluid_reduce(lbm_ctx* c, bool record);

@@ -114,6 +114,7 @@ static MhdArgs mhd_args(const lbm_ctx* c) {
     p.omega = c->relax.omega;
     p.tau_m = c->phys.tau_m;
     p.inv_tau_m = 1.0 / c->phys.tau_m;
+    p.jfac = 1.0 / (c->phys.tau_m * CSM2);
     for (int a = 0; a < 3; ++a) {
         p.g[a] = c->forcing.g[a];
         p.bw[a] = c->phys.b_wall[a];

@@ -21,6 +21,7 @@ namespace lbm {
 struct MhdArgs {
     Box box;
     double omega, inv_tau_m, tau_m;
+    double jfac;  // 1 / (tau_m c_s,m^2), the factor of the current density
     double g[3];
     double bw[3];
 };
@@ -80,7 +81,7 @@ __device__ __forceinline__ Macro<C> mhd_macro(const Moments<C>& m, const C (&g)[
         N[1][k] = (g[3][k] - g[4][k]) - (us[1] * bb[k] - bb[1] * us[k]);
         N[2][k] = (g[5][k] - g[6][k]) - (us[2] * bb[k] - bb[2] * us[k]);
     }
-    const C s = -(C)(1.0 / (p.tau_m * CSM2));
+    const C s = -(C)p.jfac;
     const C jx = s * (N[1][2] - N[2][1]);
     const C jy = s * (N[2][0] - N[0][2]);
     const C jz = s * (N[0][1] - N[1][0]);

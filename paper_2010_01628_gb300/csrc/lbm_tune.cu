@@ -167,12 +167,9 @@ extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads,
         return LBM_OK;
     }
     if (threads < 32 || threads > 256 || threads % 32 != 0) return LBM_ERR_ARG;
-    if (variant == 0 || variant == 2) {
-        if (variant == 2 && !(c->physics == LBM_PHYS_FLUID &&
-                              (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) && c->box.nx % 2 == 0 &&
-                              c->grid.wall_model == LBM_WALL_BOUNCE_BACK &&
-                              c->relax.moment_space == LBM_MOMENTS_CENTRAL && c->q == 19))
-            return LBM_ERR_UNSUPPORTED;
+    if (variant == 0 || variant == 2 || variant == 4) {
+        if (variant == 2 && !(lbm::packed16_ok(c) && c->box.nx % 2 == 0)) return LBM_ERR_UNSUPPORTED;
+        if (variant == 4 && !lbm::packed16_ok(c)) return LBM_ERR_UNSUPPORTED;
         c->variant = variant;
         c->block_x = threads;
         return LBM_OK;
@@ -239,7 +236,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
                 c->tma_stages = stages;
                 c->tma_ctas = ctas;
             } else {
-                c->variant = variant == 2 ? 2 : 0;
+                c->variant = (variant == 2 && c->box.nx % 2 == 0) || variant == 4 ? variant : 0;
             }
         }
         if (mlups) *mlups = h.count("mlups") ? h["mlups"] : 0.0;
@@ -275,10 +272,11 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
         };
         std::vector<Cand> cands;
         for (int bx : {64, 128, 256}) cands.push_back({0, bx, 0, 1});
-        if (c->physics == LBM_PHYS_FLUID && (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) &&
-            c->box.nx % 2 == 0 && c->grid.wall_model == LBM_WALL_BOUNCE_BACK &&
-            c->relax.moment_space == LBM_MOMENTS_CENTRAL && c->q == 19)
-            for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
+        if (lbm::packed16_ok(c)) {
+            if (c->box.nx % 2 == 0)
+                for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
+            for (int bx : {64, 128, 256}) cands.push_back({4, bx, 0, 1});
+        }
         for (int ctas : {1, 2, 3, 4}) {
             const int smax = lbm::fluid_tma_max_stages(c, ctas);
             for (int st : {2, 3, 4, 6, 8})

@@ -91,6 +91,20 @@ def test_16bit_two_cell_kernel(precision, shape, periodic):
     compare(r, o, TOL[precision])
 
 
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape,periodic", [((37, 10, 7), (False, False, False)), ((5, 4, 1), (False, False, False)),
+                                            ((70, 3, 4), (True, True, True)), ((33, 6, 9), (True, False, True))])
+def test_16bit_z_pair_kernel(precision, shape, periodic):
+    """Two z-neighbour nodes per thread (launch variant 4): odd nz (the last
+    thread updates one node), a single plane, walls on every side with the lid,
+    and ragged rows against the FP64 oracle."""
+    rho, u = inputs.random_fields(shape, seed=34, u_amp=0.03)
+    kw = dict(periodic=periodic, lid_u=(0.05, 0.0, 0.01), g=(1e-5, 0.0, 2e-6))
+    o = oracle_run(shape, 1.4, 20, rho, u, **kw)
+    r = gpu_run(shape, 1.4, 20, rho, u, precision=precision, launch=(4, 64, 0, 1), **kw)
+    compare(r, o, TOL[precision])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("shape,periodic,stages,ctas", [((64, 9, 7), (False, False, False), 3, 1),
                                                         ((32, 5, 6), (True, True, True), 2, 2),

@@ -97,6 +97,8 @@ def test_staged_and_paired_launches_are_refused():
             L.lbm_set_launch_shape(ctx, 1, 64, 2, 1)
         with pytest.raises(Exception):
             L.lbm_set_launch_shape(ctx, 2, 128, 0, 1)
+        with pytest.raises(Exception):
+            L.lbm_set_launch_shape(ctx, 4, 128, 0, 1)
         L.lbm_autotune(ctx, None)
         assert L.lbm_get_launch_shape(ctx)["variant"] == "direct"
     finally:

@@ -53,6 +53,8 @@ def test_launch_shapes_and_configurations():
             L.lbm_set_launch_shape(ctx, 1, 64, 2, 1)
         with pytest.raises(Exception):
             L.lbm_set_launch_shape(ctx, 2, 128, 0, 1)
+        with pytest.raises(Exception):
+            L.lbm_set_launch_shape(ctx, 4, 128, 0, 1)
         L.lbm_autotune(ctx, None)
         assert L.lbm_get_launch_shape(ctx)["variant"] == "direct"
     finally:
