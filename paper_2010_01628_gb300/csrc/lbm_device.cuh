@@ -246,6 +246,34 @@ __device__ __forceinline__ Moments<C> moments19(const C (&f)[Q]) {
     return m;
 }
 
+// moments19 from the stored values of the 16-bit formats, q_i = (f_i - w_i)/w_i,
+// without scaling each population first: the sums run over
+// 36 (f_i - w_i) = 12 q_0, 2 q_i (axes), q_i (diagonals), and the nine moments
+// the collision uses are scaled by 1/36 at the end (`moving` is left x36).
+template <typename C>
+__device__ __forceinline__ Moments<C> moments19_q(const C (&q)[Q]) {
+    Moments<C> m;
+    const C two = (C)2, k = (C)(1.0 / 36.0);
+    const C sx_p = two * q[10] + q[13] + q[14] + q[15] + q[16];
+    const C sx_m = two * q[1] + q[4] + q[5] + q[6] + q[7];
+    const C sy_p = two * q[11] + q[5] + q[13] + q[17] + q[18];
+    const C sy_m = two * q[2] + q[4] + q[8] + q[9] + q[14];
+    const C sz_p = two * q[12] + q[7] + q[9] + q[15] + q[17];
+    const C sz_m = two * q[3] + q[6] + q[8] + q[16] + q[18];
+    m.jx = (sx_p - sx_m) * k;
+    m.jy = (sy_p - sy_m) * k;
+    m.jz = (sz_p - sz_m) * k;
+    const C pxx = sx_p + sx_m, pyy = sy_p + sy_m, pzz = sz_p + sz_m;
+    m.moving = pxx + two * ((q[2] + q[11]) + (q[3] + q[12])) + ((q[8] + q[17]) + (q[9] + q[18]));
+    m.drho = ((C)12 * q[0] + m.moving) * k;
+    m.pxx_m_pyy = (pxx - pyy) * k;
+    m.pyy_m_pzz = (pyy - pzz) * k;
+    m.pxy = ((q[4] + q[13]) - (q[5] + q[14])) * k;
+    m.pxz = ((q[6] + q[15]) - (q[7] + q[16])) * k;
+    m.pyz = ((q[8] + q[17]) - (q[9] + q[18])) * k;
+    return m;
+}
+
 // Sets the rest population so that the 19 values sum to drho in the order of
 // the next step's density sum (moving directions first, f_0 last).  The
 // rounding error of f_0 = drho - S is at most half an ulp of f_0, so whenever
@@ -288,6 +316,39 @@ __device__ __forceinline__ void raw_to_populations(const C (&r)[Q], C (&f)[Q]) {
     f[18] = (r[15] + r[18] - r[9] - r[14]) * quarter;
 }
 
+// raw_to_populations with the result in the 16-bit formats' units,
+// q_i = (f_i - w_i)/w_i = 3 f_0, 18 f_i (axes), 36 f_i (diagonals): the 1/w_i
+// scaling rides on the constants of M^-1 instead of costing a multiply per
+// population.
+template <typename C>
+__device__ __forceinline__ void raw_to_populations_q(const C (&r)[Q], C (&q)[Q]) {
+    const C nine = (C)9, three = (C)3;
+    const C ax = (r[4] + (C)2 * r[5] + r[6]) * three;
+    const C ay = (r[4] - r[5] + r[6]) * three;
+    const C az = (r[4] - r[5] - (C)2 * r[6]) * three;
+    const C s1617 = r[16] + r[17], s1618 = r[16] + r[18], s1718 = r[17] + r[18];
+    q[0] = (r[0] - r[4] + r[16] + s1718) * three;
+    const C bx = (r[11] + r[13]) * nine, by = (r[10] + r[15]) * nine, bz = (r[12] + r[14]) * nine;
+    q[1] = bx - (r[1] + s1617) * nine + ax;
+    q[10] = (r[1] - s1617) * nine - bx + ax;
+    q[2] = by - (r[2] + s1618) * nine + ay;
+    q[11] = (r[2] - s1618) * nine - by + ay;
+    q[3] = bz - (r[3] + s1718) * nine + az;
+    q[12] = (r[3] - s1718) * nine - bz + az;
+    q[4] = (r[7] + r[16] - r[10] - r[11]) * nine;
+    q[5] = (r[10] + r[16] - r[7] - r[11]) * nine;
+    q[13] = (r[7] + r[10] + r[11] + r[16]) * nine;
+    q[14] = (r[11] + r[16] - r[7] - r[10]) * nine;
+    q[6] = (r[8] + r[17] - r[12] - r[13]) * nine;
+    q[7] = (r[12] + r[17] - r[8] - r[13]) * nine;
+    q[15] = (r[8] + r[12] + r[13] + r[17]) * nine;
+    q[16] = (r[13] + r[17] - r[8] - r[12]) * nine;
+    q[8] = (r[9] + r[18] - r[14] - r[15]) * nine;
+    q[9] = (r[14] + r[18] - r[9] - r[15]) * nine;
+    q[17] = (r[9] + r[14] + r[15] + r[18]) * nine;
+    q[18] = (r[15] + r[18] - r[9] - r[14]) * nine;
+}
+
 // ---------------------------------------------------------------------------
 // Back-transform of App. C in two steps, r* = N^-1 k* (Eq. rawQ19) then
 // f* = M^-1 r* (Eq. pdfQ19), for a post-collision CM vector with
@@ -298,7 +359,8 @@ __device__ __forceinline__ void raw_to_populations(const C (&r)[Q], C (&f)[Q]) {
 // f* - w directly (M^-1 maps (1,0,0,0,1,0..0,1/9,1/9,1/9) to w), so shifted
 // storage loses no digits to the O(1) rest state.  The c_s^2 factors on the
 // k5/k6 terms of r16..18 follow from the expansion c = cbar + u.
-template <typename C>
+// QOUT: the result in the 16-bit units q = (f* - w)/w (raw_to_populations_q).
+template <typename C, bool QOUT = false>
 __device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C hy, C hz, C k4, C r0c, C k4c,
                                                const C (&kd)[5], const C (&t)[6], C k16c, C k17c, C k18c,
                                                C (&f)[Q]) {
@@ -338,7 +400,10 @@ __device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C 
     r[17] = z2 * (rx2 + Ax) + x2 * Az + tx * (tz * k8 + t[3]) + tz * t[2] + k17c;
     r[18] = z2 * (ry2 + Ay) + y2 * Az + ty * (tz * k9 + t[5]) + tz * t[4] + k18c;
 
-    raw_to_populations<C>(r, f);
+    if (QOUT)
+        raw_to_populations_q<C>(r, f);
+    else
+        raw_to_populations<C>(r, f);
 }
 
 // 1/x: correctly rounded reciprocal (the FP32 division would add a slow path).
@@ -352,8 +417,9 @@ struct Macro {
 };
 
 // Single-phase forced CM collision (Sec. II.B, list after Eq. eq:posColl0),
-// in shifted variables: f holds f - w on entry and f* - w on exit.
-template <typename C>
+// in shifted variables: f holds f - w on entry and f* - w on exit (QOUT: the
+// 16-bit units (f* - w)/w on exit).
+template <typename C, bool QOUT = false>
 __device__ __forceinline__ void collide_fluid(C (&f)[Q], const Moments<C>& m, const Macro<C>& a, C omega) {
     const C rho = a.rho, ux = a.ux, uy = a.uy, uz = a.uz;
     const C hx = (C)0.5 * a.Fx, hy = (C)0.5 * a.Fy, hz = (C)0.5 * a.Fz;
@@ -371,7 +437,7 @@ __device__ __forceinline__ void collide_fluid(C (&f)[Q], const Moments<C>& m, co
     const C t[6] = {hy * third, hx * third, hz * third, hx * third, hz * third, hy * third};
     const C drho = m.drho;
     const C k16c = drho * (C)(1.0 / 9.0);
-    back_transform<C>(rho, ux, uy, uz, hx, hy, hz, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+    back_transform<C, QOUT>(rho, ux, uy, uz, hx, hy, hz, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
 }
 
 // Raw-moment variant (App. C, N = I, T = M): r* = k* from the printed list, in

@@ -94,47 +94,107 @@ struct PairCtx {
     uint32_t plane_w; // words per plane
 };
 
-// Direction I of the thread's two cells, pulled from x - c_I (shifted f - w),
-// with half-way bounce-back replacements.  Every lane of the warp executes the
-// shuffles (inactive lanes past the row end carry zeros).
-template <typename S, bool WALLS, int I>
-__device__ __forceinline__ P2 gather_pair(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
-                                          const PairCtx& t, int y, int z, float lx, float ly, float lz) {
+// The pull of direction I for the thread's two cells, in two phases so that
+// all 19 directions' loads are in flight before the first is consumed.
+// Phase 1: the thread's own word of the source row and, for a lane at the
+// warp's or the row's edge, the neighbouring word no neighbour lane holds.
+template <bool WALLS, int I>
+__device__ __forceinline__ void pair_words(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
+                                           const PairCtx& t, int y, int z, uint32_t& wv, uint32_t& ev) {
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
-    constexpr float w = (float)w_of(I);
     const int sy = cy == 0 ? y : (cy > 0 ? q.ym : q.yp);
     const int sz = cz == 0 ? z : (cz > 0 ? q.zm : q.zp);
     const bool row_wall = WALLS && ((cy > 0 && q.wym) || (cy < 0 && q.wyp) || (cz > 0 && q.wzm) || (cz < 0 && q.wzp));
-    const uint32_t* P = src + (size_t)I * t.plane_w;
-    const uint32_t row_w = (((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx) >> 1;
+    const uint32_t* P = src + (size_t)I * t.plane_w + ((((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx) >> 1);
     const uint32_t own = (uint32_t)t.x0 >> 1;
     const bool ld = t.active && !row_wall;
-    uint32_t wv = ld ? __ldg(P + row_w + own) : 0u;
+    wv = ld ? __ldg(P + own) : 0u;
+    ev = 0u;
+    if (cx > 0 && ld && (t.lane == 0 || t.x0 == 0)) ev = __ldg(P + (t.x0 == 0 ? (uint32_t)(b.nx - 2) >> 1 : own - 1));
+    if (cx < 0 && ld && (t.lane == 31 || t.x0 + 2 >= b.nx)) ev = __ldg(P + (t.x0 + 2 >= b.nx ? 0u : own + 1));
+}
+
+// Phase 2: the two cells' values of direction I, in the stored units
+// q = (f - w)/w, from the words (x-shifted directions take the neighbouring
+// half by a shuffle), with half-way bounce-back replacements.  Every lane of
+// the warp executes the shuffles (inactive lanes past the row end carry zeros).
+template <typename S, bool WALLS, int I>
+__device__ __forceinline__ P2 pair_combine(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
+                                           const PairCtx& t, uint32_t wv, uint32_t ev, float lx, float ly,
+                                           float lz) {
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
     uint32_t val = wv;
     if (cx > 0) {  // cells need elements (x0 - 1, x0)
         uint32_t pv = __shfl_up_sync(0xffffffffu, wv, 1);
-        if (t.lane == 0 || t.x0 == 0) pv = ld ? __ldg(P + row_w + (t.x0 == 0 ? (uint32_t)(b.nx - 2) >> 1 : own - 1)) : 0u;
+        if (t.lane == 0 || t.x0 == 0) pv = ev;
         val = __byte_perm(pv, wv, 0x5432);
     } else if (cx < 0) {  // cells need elements (x0 + 1, x0 + 2)
         uint32_t nv = __shfl_down_sync(0xffffffffu, wv, 1);
-        if (t.lane == 31 || t.x0 + 2 >= b.nx) nv = ld ? __ldg(P + row_w + (t.x0 + 2 >= b.nx ? 0u : own + 1)) : 0u;
+        if (t.lane == 31 || t.x0 + 2 >= b.nx) nv = ev;
         val = __byte_perm(wv, nv, 0x5432);
     }
-    P2 f = P2(Pair16<S>::lo(val), Pair16<S>::hi(val)) * P2(w);
+    P2 f = P2(Pair16<S>::lo(val), Pair16<S>::hi(val));
     if (WALLS) {
         // half-way bounce-back: the node's own post-collision population of the
         // opposite direction (+ the moving-lid term when the +y face is crossed)
+        const bool row_wall = (cy > 0 && q.wym) || (cy < 0 && q.wyp) || (cz > 0 && q.wzm) || (cz < 0 && q.wzp);
         const bool wall_a = row_wall || (cx > 0 && q.wxm);
         const bool wall_b = row_wall || (cx < 0 && t.x0 + 1 == b.nx - 1 && !(b.periodic & 1u));
         if (wall_a || wall_b) {
             const uint32_t ov = t.active ? __ldg(src + (size_t)opp_of(I) * t.plane_w + t.self_w) : 0u;
-            const float lid = (cy < 0 && q.wyp) ? (float)(6.0 * w_of(I)) * ((float)cx * lx + (float)cy * ly + (float)cz * lz)
-                                                : 0.f;
-            if (wall_a) f.v.x = Pair16<S>::lo(ov) * w + lid;
-            if (wall_b) f.v.y = Pair16<S>::hi(ov) * w + lid;
+            // the lid term 6 w c.u_lid is 6 c.u_lid in units of w
+            const float lid = (cy < 0 && q.wyp) ? 6.f * ((float)cx * lx + (float)cy * ly + (float)cz * lz) : 0.f;
+            if (wall_a) f.v.x = Pair16<S>::lo(ov) + lid;
+            if (wall_b) f.v.y = Pair16<S>::hi(ov) + lid;
         }
     }
     return f;
+}
+
+// Phase 1 for all 19 directions of plane z (row y).
+template <bool WALLS>
+__device__ __forceinline__ void pair_words_all(const uint32_t* __restrict__ src, const Box& b, const Nbr& q,
+                                               const PairCtx& t, int y, int z, uint32_t (&wv)[Q], uint32_t (&ev)[Q]) {
+#define LBM_PW(I) pair_words<WALLS, I>(src, b, q, t, y, z, wv[I], ev[I]);
+    LBM_PW(0) LBM_PW(1) LBM_PW(2) LBM_PW(3) LBM_PW(4) LBM_PW(5) LBM_PW(6) LBM_PW(7) LBM_PW(8) LBM_PW(9)
+    LBM_PW(10) LBM_PW(11) LBM_PW(12) LBM_PW(13) LBM_PW(14) LBM_PW(15) LBM_PW(16) LBM_PW(17) LBM_PW(18)
+#undef LBM_PW
+}
+
+// Phase 2 and the rest of the update of the thread's two cells: both through
+// one packed collision in the stored units q = (f - w)/w, then one 32-bit
+// store per direction.  All lanes take part in the shuffles.
+template <typename S, bool WALLS>
+__device__ __forceinline__ void pair_relax_store(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                 const FluidArgs& p, const Nbr& q, const PairCtx& t,
+                                                 const uint32_t (&wv)[Q], const uint32_t (&ev)[Q], float lx,
+                                                 float ly, float lz) {
+    const Box& b = p.box;
+    P2 f[Q];
+#define LBM_GP(I) f[I] = pair_combine<S, WALLS, I>(src, b, q, t, wv[I], ev[I], lx, ly, lz);
+    LBM_GP(0) LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9)
+    LBM_GP(10) LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
+#undef LBM_GP
+    if (!t.active) return;
+    const Moments<P2> m = moments19_q(f);
+    const Macro<P2> a = fluid_macro(m, P2((float)p.g[0]), P2((float)p.g[1]), P2((float)p.g[2]));
+    collide_fluid<P2, true>(f, m, a, P2((float)p.omega));
+#define LBM_SP(I) __stcs(dst + (size_t)I * t.plane_w + t.self_w, Pair16<S>::pack(f[I].v));
+    LBM_SP(0) LBM_SP(1) LBM_SP(2) LBM_SP(3) LBM_SP(4) LBM_SP(5) LBM_SP(6) LBM_SP(7) LBM_SP(8) LBM_SP(9)
+    LBM_SP(10) LBM_SP(11) LBM_SP(12) LBM_SP(13) LBM_SP(14) LBM_SP(15) LBM_SP(16) LBM_SP(17) LBM_SP(18)
+#undef LBM_SP
+}
+
+__device__ __forceinline__ PairCtx pair_ctx(const Box& b) {
+    PairCtx t;
+    t.x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    t.lane = threadIdx.x & 31;
+    t.active = t.x0 < b.nx;
+    t.plane_w = (uint32_t)(b.n >> 1);
+    return t;
+}
+__device__ __forceinline__ uint32_t pair_self(const Box& b, const PairCtx& t, int y, int z) {
+    return ((((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx) >> 1) + ((uint32_t)t.x0 >> 1);
 }
 
 template <typename S, bool WALLS>
@@ -144,39 +204,22 @@ __global__ void __launch_bounds__(256) fluid_step_pair_kernel(const S* __restric
     const uint32_t* src = reinterpret_cast<const uint32_t*>(src_);
     uint32_t* dst = reinterpret_cast<uint32_t*>(dst_);
     const int y = blockIdx.y, z = blockIdx.z;
-    PairCtx t;
-    t.x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    t.lane = threadIdx.x & 31;
-    t.active = t.x0 < b.nx;
-    t.plane_w = (uint32_t)(b.n >> 1);
-    t.self_w = ((((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx) >> 1) + ((uint32_t)t.x0 >> 1);
+    PairCtx t = pair_ctx(b);
+    t.self_w = pair_self(b, t, y, z);
     // x-neighbour flags of cell x0 (left wall) and of the row; the right wall
-    // of cell x0+1 is tested in gather_pair
+    // of cell x0+1 is tested in pair_combine
     const Nbr q = make_nbr(b, t.active ? t.x0 : 0, y, z);
-    const float lx = (float)p.lid[0], ly = (float)p.lid[1], lz = (float)p.lid[2];
-    P2 f[Q];
-#define LBM_GP(I) f[I] = gather_pair<S, WALLS, I>(src, b, q, t, y, z, lx, ly, lz);
-    LBM_GP(0) LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9)
-    LBM_GP(10) LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
-#undef LBM_GP
-    if (!t.active) return;
-    // both cells through one packed collision
-    const Moments<P2> m = moments19(f);
-    const Macro<P2> a = fluid_macro(m, P2((float)p.g[0]), P2((float)p.g[1]), P2((float)p.g[2]));
-    collide_fluid<P2>(f, m, a, P2((float)p.omega));
-#define LBM_SP(I) \
-    __stcs(dst + (size_t)I * t.plane_w + t.self_w, Pair16<S>::pack(P2(f[I] * P2((float)(1.0 / w_of(I)))).v));
-    LBM_SP(0) LBM_SP(1) LBM_SP(2) LBM_SP(3) LBM_SP(4) LBM_SP(5) LBM_SP(6) LBM_SP(7) LBM_SP(8) LBM_SP(9)
-    LBM_SP(10) LBM_SP(11) LBM_SP(12) LBM_SP(13) LBM_SP(14) LBM_SP(15) LBM_SP(16) LBM_SP(17) LBM_SP(18)
-#undef LBM_SP
+    uint32_t wv[Q], ev[Q];
+    pair_words_all<WALLS>(src, b, q, t, y, z, wv, ev);
+    pair_relax_store<S, WALLS>(src, dst, p, q, t, wv, ev, (float)p.lid[0], (float)p.lid[1], (float)p.lid[2]);
 }
 
 // ---------------------------------------------------------------------------
 // 16-bit storage, two nodes per thread stacked in z: (x, y, z0) and
 // (x, y, z0 + 1), z0 even (for odd nz the last thread updates z0 alone).  Every
-// pull is a plain 2-byte load of the stored q = (f - w)/w; one packed multiply
-// per direction scales both nodes to f - w, one packed collision relaxes both,
-// and one packed multiply scales back before the two stores.
+// pull is a plain 2-byte load of the stored q = (f - w)/w; one packed collision
+// relaxes both nodes in those units (the w scalings ride on the moment sums and
+// on M^-1) before the two stores.
 template <typename S, bool WALLS, int I>
 __device__ __forceinline__ float pull_q(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
                                         uint32_t self, float lx, float ly, float lz) {
@@ -205,18 +248,17 @@ __global__ void __launch_bounds__(256) fluid_step_zpair_kernel(const S* __restri
     P2 f[Q];
 #define LBM_ZP(I)                                                                                 \
     f[I] = P2(pull_q<S, WALLS, I>(src, b, qa, x, y, za, sa, lx, ly, lz),                          \
-              pull_q<S, WALLS, I>(src, b, qb, x, y, zb, sb, lx, ly, lz)) * P2((float)w_of(I));
+              pull_q<S, WALLS, I>(src, b, qb, x, y, zb, sb, lx, ly, lz));
     LBM_ZP(0) LBM_ZP(1) LBM_ZP(2) LBM_ZP(3) LBM_ZP(4) LBM_ZP(5) LBM_ZP(6) LBM_ZP(7) LBM_ZP(8) LBM_ZP(9)
     LBM_ZP(10) LBM_ZP(11) LBM_ZP(12) LBM_ZP(13) LBM_ZP(14) LBM_ZP(15) LBM_ZP(16) LBM_ZP(17) LBM_ZP(18)
 #undef LBM_ZP
-    const Moments<P2> m = moments19(f);
+    const Moments<P2> m = moments19_q(f);
     const Macro<P2> a = fluid_macro(m, P2((float)p.g[0]), P2((float)p.g[1]), P2((float)p.g[2]));
-    collide_fluid<P2>(f, m, a, P2((float)p.omega));
-#define LBM_ZS(I)                                                      \
-    {                                                                  \
-        const P2 o = f[I] * P2((float)(1.0 / w_of(I)));                \
-        Store<S>::store(dst + (size_t)I * b.n + sa, o.v.x);            \
-        if (two) Store<S>::store(dst + (size_t)I * b.n + sb, o.v.y);   \
+    collide_fluid<P2, true>(f, m, a, P2((float)p.omega));
+#define LBM_ZS(I)                                                        \
+    {                                                                    \
+        Store<S>::store(dst + (size_t)I * b.n + sa, f[I].v.x);           \
+        if (two) Store<S>::store(dst + (size_t)I * b.n + sb, f[I].v.y);  \
     }
     LBM_ZS(0) LBM_ZS(1) LBM_ZS(2) LBM_ZS(3) LBM_ZS(4) LBM_ZS(5) LBM_ZS(6) LBM_ZS(7) LBM_ZS(8) LBM_ZS(9)
     LBM_ZS(10) LBM_ZS(11) LBM_ZS(12) LBM_ZS(13) LBM_ZS(14) LBM_ZS(15) LBM_ZS(16) LBM_ZS(17) LBM_ZS(18)
