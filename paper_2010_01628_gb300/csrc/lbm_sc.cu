@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(32 * BY) sc_fused_kernel(const S* __restrict__
     }
 }
 
-// rho, u (with +F/2) and psi of a z-slab; psi of the whole box is current.// rho, u (with +F/2) and psi of a z-slab; psi of the whole box is current.
+// rho, u (with +F/2) and psi of a z-slab; psi of the whole box is current.
 template <typename S, typename C, bool WALLS>
 __global__ void sc_fields_kernel(const S* __restrict__ src, const C* __restrict__ psi, double* __restrict__ slab,
                                  ScArgs p, int z0, int nzs) {

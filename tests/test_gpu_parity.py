@@ -165,16 +165,23 @@ def sampled_oracle(u_full, rho_full, centre, k, omega, g):
     return o["rho"][r, r, r], o["u"][:, r, r, r]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
-def test_full_size_512_sampled(precision):
-    """512^3 body-force box in the benchmark's launch configuration: sampled
-    nodes (corners and edges included) against the oracle's dependency cone."""
+@pytest.mark.parametrize("precision,launch", [("fp32", "auto"), ("fp16", None), ("fp16", "auto"), ("bf16", None),
+                                              ("bf16", "auto"), ("bf16", (4, 128, 0, 1))])
+def test_full_size_512_sampled(precision, launch):
+    """512^3 body-force box in the benchmark's launch configuration (the
+    autotuner's choice, as bench.py runs it; for 16-bit storage also the
+    default one-node kernel and the z-pair kernel): sampled nodes (corners and
+    edges included) against the oracle's dependency cone."""
     from paper_2010_01628_gb300 import binding as L
     n, k = 512, 4
     omega, g = 1 / 0.6, (1e-6, 0.0, 0.0)
     rho, u = inputs.noise_box((n, n, n), amp=1e-3, seed=1)
     ctx = L.lbm_create((n, n, n), omega, g=g, precision=precision)
     try:
+        if launch == "auto":
+            L.lbm_autotune(ctx, None)
+        elif launch is not None:
+            L.lbm_set_launch_shape(ctx, *launch)
         L.lbm_init_fields(ctx, rho, u)
         L.lbm_step(ctx, k)
         out = L.lbm_fields(ctx, (n, n, n))
