@@ -226,11 +226,11 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
     if only in (None, "mhd_batch"):
         out.update(_mhd_batch(L, timed, steps, peak, domains, tune_cache, ranks))
     if only in (None, "cgm"):
-        out.update(_cgm(L, timed, steps, peak, n_cgm))
+        out.update(_cgm(L, timed, steps, peak, n_cgm, launch))
     if only in (None, "sc"):
         out.update(_sc(L, timed, steps, peak, (n_only,) if n_only else (100, 256), launch))
     if only in (None, "rt"):
-        out.update(_rt(L, timed, steps, peak))
+        out.update(_rt(L, timed, steps, peak, launch))
     if only in (None, "appd"):
         out.update(_appd(L, timed, steps, n_only or 256))
     if only in (None, "channel"):
@@ -299,9 +299,9 @@ def _mhd_batch(L, timed, steps, peak, domains, tune_cache="tmp", ranks=None):
     return out
 
 
-def _cgm(L, timed, steps, peak, n):
+def _cgm(L, timed, steps, peak, n, launch="auto"):
     out = {}
-    # C4: colour-gradient droplets n^3 (10% volume, R in [8,24]), FP32.
+    # C4: colour-gradient droplets n^3 (10% volume, R in [8,24]), FP32, autotuned block size.
     rho, u, phase, spheres, frac = inputs.droplets(n, seed=3)
     sigma, tau = 1e-4, 0.8
     alpha_b = 1 / 3
@@ -309,6 +309,8 @@ def _cgm(L, timed, steps, peak, n):
     c = L.lbm_create((n, n, n), 1 / tau, physics="cgm", precision="fp32", alpha_r=alpha_r, alpha_b=alpha_b,
                      A=9 * sigma / tau / 4, beta=0.7)
     L.lbm_init_fields(c, rho, u, phase=phase)
+    tuned = L.lbm_autotune(c, None) if launch == "auto" else apply_launch(L, c, launch, None)
+    shape = L.lbm_get_launch_shape(c)
     L.lbm_step(c, 3)
     n_c = max(20, steps // 2)
     t = timed(lambda k: L.lbm_step(c, k), n_c)
@@ -317,7 +319,8 @@ def _cgm(L, timed, steps, peak, n):
     ach = 312 * n ** 3 * n_c / t / 1e9
     out[f"cgm_droplets_{n}"] = {"MLUPS": n ** 3 * n_c / t / 1e6, "steps": n_c, "droplets": len(spheres),
                                "volume_fraction": frac, "bytes_per_lup": 312, "moved_bytes_per_lup": 464,
-                               "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
+                               "launch": shape, "autotune_MLUPS": tuned, "achieved_GBps": ach,
+                               "frac_of_hbm_peak": ach / peak,
                                "note": "two passes per step (phase field, then collide); 312 B/LUP algorithmic"}
     return out
 
@@ -352,7 +355,7 @@ def _sc(L, timed, steps, peak, sizes=(100, 256), launch="auto"):
     return out
 
 
-def _rt(L, timed, steps, peak):
+def _rt(L, timed, steps, peak, launch="auto"):
     # Rayleigh-Taylor (Sec. III.H) on the colour-gradient step: 64 x 256 x 64, rho 3 over 1, Re 512, At 0.5,
     # walls at bottom and top, F = (rho - 2) g, FP32.  Timed from t = 0 (the interface is still flat-ish).
     W = 64
@@ -363,6 +366,8 @@ def _rt(L, timed, steps, peak):
     c = L.lbm_create(shape, 1 / (3 * nu + 0.5), periodic=(True, False, True), g=(0.0, -g, 0.0), rho_ref=2.0,
                      physics="cgm", precision="fp32", alpha_r=7 / 9, alpha_b=1 / 3, A=0.0, beta=0.7)
     L.lbm_init_fields(c, rho, u, phase=phase)
+    tuned = L.lbm_autotune(c, None) if launch == "auto" else apply_launch(L, c, launch, None)
+    shape_l = L.lbm_get_launch_shape(c)
     L.lbm_step(c, 3)
     n_c = max(20, steps // 2) * 4
     t = timed(lambda k: L.lbm_step(c, k), n_c)
@@ -372,7 +377,7 @@ def _rt(L, timed, steps, peak):
     ach = 312 * cells * n_c / t / 1e9
     return {"cgm_rayleigh_taylor_64x256x64": {
         "MLUPS": cells * n_c / t / 1e6, "steps": n_c, "bytes_per_lup": 312, "moved_bytes_per_lup": 464,
-        "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
+        "launch": shape_l, "autotune_MLUPS": tuned, "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak,
         "note": "colour-gradient two-pass step with walls; 312 B/LUP algorithmic"}}
 
 
@@ -491,7 +496,7 @@ def run_ours(args):
     if args.only:
         peak, _ = measured_peaks()
         res = extra_workloads(L, torch, stream, args.steps, peak, only=args.only, domains=args.domains,
-                              n_cgm=args.n, tune_cache=args.tune_cache,
+                              n_cgm=args.n if args.n != N else 256, tune_cache=args.tune_cache,
                               n_only=args.n if args.n != N else None, ranks=ranks, launch=args.launch)
         if rank == 0:
             print(json.dumps({"only": args.only, "workloads": res}), flush=True)
@@ -606,7 +611,7 @@ def main():
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")
     ap.add_argument("--launch", default="auto",
-                    help="launch shape of the single-phase step: auto | direct[:threads] | pair[:threads] | "
+                    help="launch shape: auto | direct[:threads] | pair[:threads] | "
                          "zpair[:threads] | tma:stages:ctas | fused:threads:planes")
     ap.add_argument("--tune-cache", default="tmp", choices=["tmp", "none"],
                     help="autotuner cache of the batch workload: a file in the temp dir, or none")
