@@ -197,7 +197,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(N, "fp64") | {"sample": f"{n}^3"},
+            "config": workload_config(N, "fp32") | {"sample": f"{n}^3",
+                                                     "oracle": "FP64 closed-form oracle on the sample (dtype f64)"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": f"{n}^3 periodic sample of the {N}^3 workload per step"},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
