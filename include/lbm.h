@@ -221,6 +221,13 @@ lbm_status lbm_batch_info(const lbm_ctx *batch, int *threads, int *grid, int *gr
  * and reports the status word the kernel wrote (LBM_ERR_TIMEOUT expected). */
 lbm_status lbm_barrier_selftest(double timeout_s, int *observed);
 
+/* Diagnostic of the bounded mbarrier wait of the TMA-staged kernels (launch
+ * variant 1): one thread waits for an mbarrier phase with the given limit
+ * (0 < timeout_s <= 10).  arrive = 0: nothing completes the phase and the wait
+ * must give up (LBM_ERR_TIMEOUT in *observed); arrive != 0: the thread arrives
+ * first and the wait must succeed (LBM_OK).  The device stays usable. */
+lbm_status lbm_mbarrier_selftest(double timeout_s, int arrive, int *observed);
+
 /* ---- Autotuner ---------------------------------------------------------------
  * Chooses the launch shape of a context by timed trials that leave its state
  * unchanged: threads per block of the single-domain step kernels, or threads

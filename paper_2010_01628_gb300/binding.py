@@ -378,6 +378,16 @@ def lbm_barrier_selftest(timeout_s=0.2):
     return obs.value
 
 
+_lib.lbm_mbarrier_selftest.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+_lib.lbm_mbarrier_selftest.restype = ctypes.c_int
+
+
+def lbm_mbarrier_selftest(timeout_s=0.2, arrive=False):
+    obs = ctypes.c_int()
+    _check(_lib.lbm_mbarrier_selftest(float(timeout_s), 1 if arrive else 0, ctypes.byref(obs)))
+    return obs.value
+
+
 _lib.lbm_set_launch_shape.argtypes = [_V, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.lbm_set_launch_shape.restype = ctypes.c_int
 

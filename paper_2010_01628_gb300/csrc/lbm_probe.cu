@@ -1,8 +1,10 @@
 // lbm_probe.cu -- arithmetic-throughput probe used as the denominator of the
 // FP64 step's ALU roofline: independent FMA chains (8 per thread), one store
-// per thread, timed with CUDA events.
+// per thread, timed with CUDA events.  Also the self-test of the bounded
+// mbarrier wait that the TMA-staged kernels use.
 #include <cuda_runtime.h>
 
+#include "lbm_device.cuh"
 #include "lbm_internal.h"
 
 namespace {
@@ -53,7 +55,43 @@ cudaError_t rate(int iters, double* fma_per_s) {
     return e;
 }
 
+// One thread waits (bounded) for phase 0 of an mbarrier expecting one arrival;
+// with `arrive` it arrives first and the wait must succeed at once, without it
+// nothing completes the phase and the wait must give up after limit_ns.
+__global__ void mbar_selftest_kernel(unsigned long long limit_ns, int arrive, int* __restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    lbm::mbar_init(&bar, 1);
+    lbm::fence_barrier_init();
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(lbm::smem_u32(&bar)) : "memory");
+    *status = lbm::mbar_wait_bounded(&bar, 0, limit_ns) ? (int)LBM_OK : (int)LBM_ERR_TIMEOUT;
+}
+
 }  // namespace
+
+extern "C" lbm_status lbm_mbarrier_selftest(double timeout_s, int arrive, int* observed) {
+    if (!observed || !(timeout_s > 0.0) || timeout_s > 10.0) return LBM_ERR_ARG;
+    int* st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
+    cudaError_t e = cudaMemset(st, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        mbar_selftest_kernel<<<1, 32>>>((unsigned long long)(timeout_s * 1e9), arrive ? 1 : 0, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int h = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    *observed = h;
+    return LBM_OK;
+}
 
 extern "C" lbm_status lbm_probe_fma_rate(double* fp64_fma_per_s, double* fp32_fma_per_s) {
     if (!fp64_fma_per_s || !fp32_fma_per_s) return LBM_ERR_ARG;

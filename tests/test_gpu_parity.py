@@ -120,6 +120,24 @@ def test_tma_staged_kernel(precision, shape, periodic, stages, ctas):
     compare(r, o, TOL[precision])
 
 
+def test_tma_wait_limit_reports_timeout_and_device_stays_usable():
+    """The bounded mbarrier wait of the TMA-staged kernels: with no arrival the
+    wait gives up after its limit and the kernel reports LBM_ERR_TIMEOUT; with
+    the arrival it succeeds at once; a staged step still matches the oracle
+    afterwards."""
+    import time
+    from paper_2010_01628_gb300 import binding as L
+    t = time.perf_counter()
+    assert L.lbm_mbarrier_selftest(0.2, arrive=False) == L.LBM_ERR_TIMEOUT
+    assert time.perf_counter() - t >= 0.2
+    assert L.lbm_mbarrier_selftest(0.2, arrive=True) == L.LBM_OK
+    shape = (32, 5, 6)
+    rho, u = inputs.random_fields(shape, seed=36, u_amp=0.03)
+    o = oracle_run(shape, 1.45, 8, rho, u)
+    r = gpu_run(shape, 1.45, 8, rho, u, precision="fp32", launch=(1, 64, 2, 1))
+    compare(r, o, TOL["fp32"])
+
+
 def test_launch_shapes_agree_bitwise_fp64():
     """Direct-pull and TMA-staged kernels compute the same arithmetic."""
     shape = (40, 12, 10)
