@@ -187,7 +187,11 @@ lbm_status lbm_sync(lbm_ctx *ctx);
 /* Raw population storage (checkpoint/restart).  Size in bytes of one copy of
  * the state; the layout is the storage format (structure of arrays, planes of
  * n values in direction order, the stored quantity as documented for
- * lbm_precision; MHD appends 21 magnetic planes, CGM stores red then blue).
+ * lbm_precision; MHD appends 21 magnetic planes.  CGM stores 24 unshifted
+ * planes: the 19 total populations f_i, then per node the red fraction
+ * a = rho_r / rho, the recolouring vector V (3 planes) and the red rest
+ * population; the red population of moving direction i is a f_i + kappa_i c_i.V
+ * with kappa = 1/12 (axes) or 1/(24 sqrt 2) (diagonals), blue the rest).
  * dst/src may be host or device pointers. */
 size_t lbm_state_bytes(const lbm_ctx *ctx);
 lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);

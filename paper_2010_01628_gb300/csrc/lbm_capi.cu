@@ -270,7 +270,7 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->elem = precision == LBM_FP64 ? 8 : (precision == LBM_FP32 ? 4 : 2);
     c->q = lattice == LBM_D3Q27 ? 27 : 19;
     c->planes = c->q == 27 ? 27
-                           : ((physics == LBM_PHYS_FLUID || physics == LBM_PHYS_SC) ? 19 : (physics == LBM_PHYS_MHD ? 40 : 38));
+                           : ((physics == LBM_PHYS_FLUID || physics == LBM_PHYS_SC) ? 19 : (physics == LBM_PHYS_MHD ? 40 : 24));
     c->alloc = g_alloc;
     c->release = g_release;
     c->user = g_user;
@@ -291,7 +291,8 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
     c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
     const bool has_phi = physics == LBM_PHYS_CGM || physics == LBM_PHYS_SC;
-    if (has_phi) c->phi = dev_alloc(c, c->box.n * cb);
+    // scratch: psi (Shan-Chen); phi and the red density (colour gradient)
+    if (has_phi) c->phi = dev_alloc(c, (physics == LBM_PHYS_CGM ? 2 : 1) * c->box.n * cb);
     c->status = (int*)dev_alloc(c, 256);
     bool ok = c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging && c->status &&
               (!has_phi || c->phi);

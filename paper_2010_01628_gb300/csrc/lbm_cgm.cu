@@ -1,8 +1,8 @@
 // lbm_cgm.cu -- colour-gradient two-phase step (App. E of arXiv:2010.01628).
 //
-// Two passes per step.  Pass 1 pulls the red and blue populations of every
-// node and writes the order parameter phi = (rho_r - rho_b)/(rho_r + rho_b)
-// (Eq. eq:order).  Pass 2 pulls them again, collides the total populations in
+// Two passes per step.  Pass 1 pulls the populations of every node and writes
+// the order parameter phi = (rho_r - rho_b)/(rho_r + rho_b) (Eq. eq:order) and
+// the red density.  Pass 2 pulls again, collides the total populations in
 // central-moment space toward h_eq (App. E post-collision list, with the 1/6 on
 // k16..18 that makes it reduce to rho c_s^4 at alpha = 1/3), adds the
 // surface-tension perturbation with the squared projection (c_i . grad phi)^2
@@ -11,7 +11,15 @@
 // stencil (1/c_s^2) sum_i w_i c_i phi(x + c_i); a neighbour behind a wall
 // contributes the node's own phi.
 //
-// Storage: planes 0..18 red, 19..37 blue, unshifted.
+// Storage, 24 planes per copy, unshifted: 0..18 the total populations f_i;
+// then, per node, the red fraction a = rho_r / rho and the recolouring vector
+// V = beta (rho_r rho_b / rho) (1 - alpha) grad phi / |grad phi| of its last
+// collision, and its red rest population.  The recolouring makes the red
+// population of a moving direction a f_i + e_i with
+// e_i = beta (rho_r rho_b / rho) cos(theta_i) phi_i(alpha) = kappa_i c_i . V
+// (kappa = 1/12 on the axes, 1/(24 sqrt 2) on the diagonals), so it is rebuilt
+// where it is pulled instead of stored, and blue is the total minus red: a
+// step moves 24 + 24 values per node instead of 2 x 19 + 2 x 19.
 #include "lbm_internal.h"
 #include "lbm_reduce.cuh"
 
@@ -29,9 +37,12 @@ struct CgmNode {
     C rho_r, rho_b, rho, ux, uy, uz, Fx, Fy, Fz, alpha;
 };
 
-// Colour density: the 18 moving populations in direction order, then the rest
-// population.  The store below writes f_0 = rho_c - (that same moving sum), so
-// a uniform region sums back to its colour density exactly in FP32.
+constexpr int CGM_FRAC = Q, CGM_VX = Q + 1, CGM_VY = Q + 2, CGM_VZ = Q + 3, CGM_RED0 = Q + 4;
+
+// Density of a population set: the 18 moving populations in direction order,
+// then the rest population.  The stores below write the rest population as the
+// density minus that same moving sum, so a uniform region sums back to its
+// density (and its red density) exactly in FP32.
 template <typename C>
 __device__ __forceinline__ C colour_sum(const C (&f)[Q]) {
     C s = f[1];
@@ -40,17 +51,71 @@ __device__ __forceinline__ C colour_sum(const C (&f)[Q]) {
     return s + f[0];
 }
 
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Red population of moving direction J at a node with red fraction a,
+// recolouring vector V and total population f: a f + kappa_J c_J . V.  The
+// collision that stores (f, a, V) and the pull that rebuilds it run this same
+// sequence of roundings, so the red rest population stored for the mass
+// balance matches the pulled red populations exactly.
+template <typename C, int J>
+__device__ __forceinline__ C red_pop(C a, C vx, C vy, C vz, C f) {
+    constexpr int cx = cx_of(J), cy = cy_of(J), cz = cz_of(J);
+    constexpr double kappa = cx * cx + cy * cy + cz * cz == 1 ? 1.0 / 12.0 : 0.70710678118654752440 / 24.0;
+    C cv = (C)0;
+    if (cx) cv = cx > 0 ? vx : -vx;
+    if (cy) cv = cx ? (cy > 0 ? cv + vy : cv - vy) : (cy > 0 ? vy : -vy);
+    if (cz) cv = (cx || cy) ? (cz > 0 ? cv + vz : cv - vz) : (cz > 0 ? vz : -vz);
+    return fma_rn(a, f, (C)kappa * cv);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ C cgm_ld(const S* __restrict__ src, size_t n, int plane, uint32_t cell) {
+    return (C)Store<S>::load(src + (size_t)plane * n + cell);
+}
+
+// Pull of moving direction I: the total population f_I(x) = f*_I(x - c_I) and
+// its red part, rebuilt from the source node's red fraction and recolouring
+// vector; from behind a wall, the node's own opposite direction (half-way
+// bounce-back; the colour-gradient step has no moving lid).
+template <typename S, typename C, bool WALLS, int I>
+__device__ __forceinline__ void cgm_pull(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
+                                         uint32_t self, C& f, C& r) {
+    uint32_t cell;
+    const bool wall = pull_source<I>(b, q, x, y, z, cell);
+    if (!WALLS || !wall) {
+        f = cgm_ld<S, C>(src, b.n, I, cell);
+        r = red_pop<C, I>(cgm_ld<S, C>(src, b.n, CGM_FRAC, cell), cgm_ld<S, C>(src, b.n, CGM_VX, cell),
+                          cgm_ld<S, C>(src, b.n, CGM_VY, cell), cgm_ld<S, C>(src, b.n, CGM_VZ, cell), f);
+    } else {
+        constexpr int J = opp_of(I);
+        f = cgm_ld<S, C>(src, b.n, J, self);
+        r = red_pop<C, J>(cgm_ld<S, C>(src, b.n, CGM_FRAC, self), cgm_ld<S, C>(src, b.n, CGM_VX, self),
+                          cgm_ld<S, C>(src, b.n, CGM_VY, self), cgm_ld<S, C>(src, b.n, CGM_VZ, self), f);
+    }
+}
+
+// All 19 pulled populations of a node and their red parts.
+template <typename S, typename C, bool WALLS>
+__device__ __forceinline__ void cgm_pull_all(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y,
+                                             int z, uint32_t self, C (&f)[Q], C (&r)[Q]) {
+    f[0] = cgm_ld<S, C>(src, b.n, 0, self);
+    r[0] = cgm_ld<S, C>(src, b.n, CGM_RED0, self);
+#define LBM_CP(I) cgm_pull<S, C, WALLS, I>(src, b, q, x, y, z, self, f[I], r[I]);
+    LBM_CP(1) LBM_CP(2) LBM_CP(3) LBM_CP(4) LBM_CP(5) LBM_CP(6) LBM_CP(7) LBM_CP(8) LBM_CP(9) LBM_CP(10)
+    LBM_CP(11) LBM_CP(12) LBM_CP(13) LBM_CP(14) LBM_CP(15) LBM_CP(16) LBM_CP(17) LBM_CP(18)
+#undef LBM_CP
+}
+
+// rho, F = rho g - rho_ref g and u = (sum f c + F/2)/rho of pulled totals
+// (rho summed as colour_sum), with the colour densities rho_r and rho - rho_r.
 template <typename C>
-__device__ __forceinline__ CgmNode<C> cgm_macro(const C (&fr)[Q], const C (&fb)[Q], C (&f)[Q], Moments<C>& m,
-                                                const CgmArgs& p) {
+__device__ __forceinline__ CgmNode<C> cgm_macro(const C (&f)[Q], const Moments<C>& m, C rho_r, const CgmArgs& p) {
     CgmNode<C> s;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = fr[i] + fb[i];
-    m = moments19(f);
-    const C sr = colour_sum(fr), sb = colour_sum(fb);
-    s.rho_r = sr;
-    s.rho_b = sb;
-    s.rho = sr + sb;
+    s.rho = colour_sum(f);
+    s.rho_r = rho_r;
+    s.rho_b = s.rho - rho_r;
     s.Fx = s.rho * (C)p.g[0] - (C)p.rg[0];
     s.Fy = s.rho * (C)p.g[1] - (C)p.rg[1];
     s.Fz = s.rho * (C)p.g[2] - (C)p.rg[2];
@@ -58,7 +123,7 @@ __device__ __forceinline__ CgmNode<C> cgm_macro(const C (&fr)[Q], const C (&fb)[
     s.ux = (m.jx + (C)0.5 * s.Fx) * inv;
     s.uy = (m.jy + (C)0.5 * s.Fy) * inv;
     s.uz = (m.jz + (C)0.5 * s.Fz) * inv;
-    s.alpha = (sr * (C)p.alpha_r + sb * (C)p.alpha_b) * inv;
+    s.alpha = (s.rho_r * (C)p.alpha_r + s.rho_b * (C)p.alpha_b) * inv;
     return s;
 }
 
@@ -96,19 +161,21 @@ __device__ __forceinline__ void cgm_collide(C (&f)[Q], const Moments<C>& m, cons
     back_transform<C>(rho, ux, uy, uz, hx, hy, hz, k4, rho, k4, kd, t, k16, k17, k18, f);
 }
 
+// Pass 1: phi and rho_r of every node from its pulled populations.
 template <typename S, typename C, bool WALLS>
-__global__ void __launch_bounds__(256) cgm_phi_kernel(const S* __restrict__ src, C* __restrict__ phi, CgmArgs p) {
+__global__ void __launch_bounds__(256) cgm_phi_kernel(const S* __restrict__ src, C* __restrict__ phi,
+                                                      C* __restrict__ rho_red, CgmArgs p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     const Box& b = p.box;
     if (x >= b.nx) return;
     const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
     const Nbr q = make_nbr(b, x, y, z);
-    C fr[Q], fb[Q];
-    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
-    gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
-    const C sr = colour_sum(fr), sb = colour_sum(fb);
-    phi[self] = (sr - sb) / (sr + sb);
+    C f[Q], r[Q];
+    cgm_pull_all<S, C, WALLS>(src, b, q, x, y, z, self, f, r);
+    const C sr = colour_sum(r), st = colour_sum(f);
+    phi[self] = (sr - (st - sr)) / st;
+    rho_red[self] = sr;
 }
 
 template <typename C>
@@ -121,49 +188,44 @@ __device__ __forceinline__ void grad_phi(const C* __restrict__ phi, const Box& b
     gr[2] = (C)3 * s[2];
 }
 
-// Direction I (1..18) of the perturbed, recoloured populations; stores them
-// and adds them to the running colour sums (the rest direction is stored last
-// from the colour mass balance).
+// Direction I (1..18) after the collision: adds the perturbation, stores the
+// total population and adds it and its red part to the running sums.
 template <typename S, typename C, int I>
-__device__ __forceinline__ void perturb_recolour_store(S* __restrict__ dst, size_t n, uint32_t self, C fi,
-                                                       const C (&gr)[3], C n2, C pert_amp, C inv_n2, C inv_nrm,
-                                                       C frac_r, C frac_b, C sep, C alpha, C& sum_r, C& sum_b) {
+__device__ __forceinline__ void perturb_store(S* __restrict__ dst, size_t n, uint32_t self, C fi, const C (&gr)[3],
+                                              C n2, C pert_amp, C inv_n2, C a, const C (&v)[3], C& sum_f, C& sum_r) {
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
     constexpr int c2 = cx * cx + cy * cy + cz * cz;
-    const C cg = (C)cx * gr[0] + (C)cy * gr[1] + (C)cz * gr[2];
     if (n2 > (C)1e-24) {
-        const C Bi = c2 == 0 ? (C)(-1.0 / 3.0) : (c2 == 1 ? (C)(1.0 / 18.0) : (C)(1.0 / 36.0));
+        const C cg = (C)cx * gr[0] + (C)cy * gr[1] + (C)cz * gr[2];
+        const C Bi = c2 == 1 ? (C)(1.0 / 18.0) : (C)(1.0 / 36.0);
         fi += pert_amp * ((C)w_of(I) * cg * cg * inv_n2 - Bi);
     }
-    C cos_t = (C)0;
-    if (c2 > 0 && inv_nrm > (C)0) cos_t = cg * inv_nrm * (C)(c2 == 1 ? 1.0 : 0.70710678118654752440);
-    const C e = sep * cos_t * cgm_phi_i<C, I>(alpha);
-    const C vr = frac_r * fi + e, vb = frac_b * fi - e;
-    Store<S>::store(dst + (size_t)I * n + self, vr);
-    Store<S>::store(dst + (size_t)(Q + I) * n + self, vb);
+    Store<S>::store(dst + (size_t)I * n + self, fi);
+    const C ri = red_pop<C, I>(a, v[0], v[1], v[2], fi);
     if (I == 1) {
-        sum_r = vr;
-        sum_b = vb;
+        sum_f = fi;
+        sum_r = ri;
     } else {
-        sum_r += vr;
-        sum_b += vb;
+        sum_f += fi;
+        sum_r += ri;
     }
 }
 
+// Pass 2: pull, collide the totals, perturb, recolour.
 template <typename S, typename C, bool WALLS>
 __global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                          const C* __restrict__ phi, CgmArgs p) {
+                                                          const C* __restrict__ phi, const C* __restrict__ rho_red,
+                                                          CgmArgs p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     const Box& b = p.box;
     if (x >= b.nx) return;
     const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
     const Nbr q = make_nbr(b, x, y, z);
-    C fr[Q], fb[Q], f[Q];
-    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
-    gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
-    Moments<C> m;
-    const CgmNode<C> s = cgm_macro<C>(fr, fb, f, m, p);
+    C f[Q];
+    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, f);
+    const Moments<C> m = moments19(f);
+    const CgmNode<C> s = cgm_macro<C>(f, m, rho_red[self], p);
     cgm_collide<C>(f, m, s, (C)p.omega);
     C gr[3];
     grad_phi<C>(phi, b, q, x, y, z, self, gr);
@@ -174,20 +236,23 @@ __global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ 
     const C inv_n2 = n2 > (C)1e-24 ? (C)1 / n2 : (C)0;
     const C inv_nrm = nrm > (C)1e-12 ? (C)1 / nrm : (C)0;
     const C inv_rho = recip(s.rho);
-    const C frac_r = s.rho_r * inv_rho, frac_b = s.rho_b * inv_rho;
-    // beta rho_r rho_b / rho^2 * g_eq(rho, 0) with g_eq = rho phi_i(alpha)
-    const C sep = (C)p.beta * s.rho_r * s.rho_b * inv_rho;
-    C sum_r, sum_b;
-#define LBM_PR(I)                                                                                             \
-    perturb_recolour_store<S, C, I>(dst, b.n, self, f[I], gr, n2, pert_amp, inv_n2, inv_nrm, frac_r, frac_b, sep, \
-                                    s.alpha, sum_r, sum_b);
-    LBM_PR(1) LBM_PR(2) LBM_PR(3) LBM_PR(4) LBM_PR(5) LBM_PR(6) LBM_PR(7) LBM_PR(8) LBM_PR(9)
-    LBM_PR(10) LBM_PR(11) LBM_PR(12) LBM_PR(13) LBM_PR(14) LBM_PR(15) LBM_PR(16) LBM_PR(17) LBM_PR(18)
-#undef LBM_PR
-    // Rest direction: colour mass balance (perturbation and recolouring conserve
-    // each colour, and cos(theta_0) = 0).
-    Store<S>::store(dst + self, s.rho_r - sum_r);
-    Store<S>::store(dst + (size_t)Q * b.n + self, s.rho_b - sum_b);
+    // recolouring: red fraction rho_r / rho, and V = beta rho_r rho_b / rho (1 - alpha) grad phi / |grad phi|
+    const C a = s.rho_r * inv_rho;
+    const C w = (C)p.beta * s.rho_r * s.rho_b * inv_rho * ((C)1 - s.alpha) * inv_nrm;
+    const C v[3] = {w * gr[0], w * gr[1], w * gr[2]};
+    C sum_f, sum_r;
+#define LBM_PS(I) perturb_store<S, C, I>(dst, b.n, self, f[I], gr, n2, pert_amp, inv_n2, a, v, sum_f, sum_r);
+    LBM_PS(1) LBM_PS(2) LBM_PS(3) LBM_PS(4) LBM_PS(5) LBM_PS(6) LBM_PS(7) LBM_PS(8) LBM_PS(9)
+    LBM_PS(10) LBM_PS(11) LBM_PS(12) LBM_PS(13) LBM_PS(14) LBM_PS(15) LBM_PS(16) LBM_PS(17) LBM_PS(18)
+#undef LBM_PS
+    // Rest direction from the mass balances (the perturbation and the
+    // recolouring conserve each colour; cos(theta_0) = 0).
+    Store<S>::store(dst + self, s.rho - sum_f);
+    Store<S>::store(dst + (size_t)CGM_RED0 * b.n + self, s.rho_r - sum_r);
+    Store<S>::store(dst + (size_t)CGM_FRAC * b.n + self, a);
+    Store<S>::store(dst + (size_t)CGM_VX * b.n + self, v[0]);
+    Store<S>::store(dst + (size_t)CGM_VY * b.n + self, v[1]);
+    Store<S>::store(dst + (size_t)CGM_VZ * b.n + self, v[2]);
 }
 
 template <typename S, typename C>
@@ -227,18 +292,20 @@ __global__ void cgm_init_kernel(S* __restrict__ dst, const double* __restrict__ 
     mz.pyz = r * s.uy * s.uz;
     C h[Q];
     cgm_collide<C>(h, mz, s, (C)0);  // omega = 0 keeps kd = k5..9 = 0 exactly
-    const C fr = (C)(rr / rho), fbl = (C)(rb / rho);
-    C sum_r = (C)0, sum_b = (C)0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const C vr = fr * h[i], vb = fbl * h[i];
-        Store<S>::store(dst + (size_t)i * b.n + self, vr);
-        Store<S>::store(dst + (size_t)(Q + i) * b.n + self, vb);
-        sum_r += vr;
-        sum_b += vb;
-    }
-    Store<S>::store(dst + self, s.rho_r - sum_r);
-    Store<S>::store(dst + (size_t)Q * b.n + self, s.rho_b - sum_b);
+    // each colour takes its density fraction of h_eq: red fraction rr / rho, V = 0
+    const C a = (C)(rr / rho), zero = (C)0;
+    const C v[3] = {zero, zero, zero};
+    C sum_f, sum_r;
+#define LBM_IS(I) perturb_store<S, C, I>(dst, b.n, self, h[I], v, zero, zero, zero, a, v, sum_f, sum_r);
+    LBM_IS(1) LBM_IS(2) LBM_IS(3) LBM_IS(4) LBM_IS(5) LBM_IS(6) LBM_IS(7) LBM_IS(8) LBM_IS(9)
+    LBM_IS(10) LBM_IS(11) LBM_IS(12) LBM_IS(13) LBM_IS(14) LBM_IS(15) LBM_IS(16) LBM_IS(17) LBM_IS(18)
+#undef LBM_IS
+    Store<S>::store(dst + self, s.rho - sum_f);
+    Store<S>::store(dst + (size_t)CGM_RED0 * b.n + self, s.rho_r - sum_r);
+    Store<S>::store(dst + (size_t)CGM_FRAC * b.n + self, a);
+    Store<S>::store(dst + (size_t)CGM_VX * b.n + self, zero);
+    Store<S>::store(dst + (size_t)CGM_VY * b.n + self, zero);
+    Store<S>::store(dst + (size_t)CGM_VZ * b.n + self, zero);
 }
 
 template <typename S, typename C, bool WALLS>
@@ -252,11 +319,10 @@ __global__ void cgm_fields_kernel(const S* __restrict__ src, double* __restrict_
     const size_t k = ((size_t)zs * b.ny + y) * b.nx + x;
     const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
     const Nbr q = make_nbr(b, x, y, z);
-    C fr[Q], fb[Q], f[Q];
-    gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
-    gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
-    Moments<C> mo;
-    const CgmNode<C> s = cgm_macro<C>(fr, fb, f, mo, p);
+    C f[Q], r[Q];
+    cgm_pull_all<S, C, WALLS>(src, b, q, x, y, z, self, f, r);
+    const Moments<C> mo = moments19(f);
+    const CgmNode<C> s = cgm_macro<C>(f, mo, colour_sum(r), p);
     slab[k] = (double)s.rho;
     slab[m + k] = (double)s.ux;
     slab[2 * m + k] = (double)s.uy;
@@ -281,11 +347,11 @@ __global__ void __launch_bounds__(RED_THREADS) cgm_reduce_kernel(const S* __rest
         if (x < b.nx) {
             const uint32_t self = ((uint32_t)z * (uint32_t)b.ny + (uint32_t)y) * (uint32_t)b.nx + (uint32_t)x;
             const Nbr q = make_nbr(b, x, y, z);
-            C fr[Q], fb[Q], f[Q];
-            gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, fr);
-            gather19<S, C, WALLS>(src + (size_t)Q * b.n, b, q, x, y, z, self, (C)0, (C)0, (C)0, fb);
-            Moments<C> mo;
-            const CgmNode<C> s = cgm_macro<C>(fr, fb, f, mo, p);
+            C f[Q];
+            gather19<S, C, WALLS>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, f);
+            const Moments<C> mo = moments19(f);
+            // rho and u need only the totals (the force is rho g - rho_ref g)
+            const CgmNode<C> s = cgm_macro<C>(f, mo, (C)0, p);
             reduce_node<C>(acc, s.rho, s.ux, s.uy, s.uz, uprev, b.n, self, have_prev, record);
         }
     }
@@ -315,15 +381,16 @@ static cudaError_t step_t(lbm_ctx* c, long n, bool dry) {
     const int bx = c->block_x;
     const dim3 grid = step_grid(c->box, bx);
     C* phi = (C*)c->phi;
+    C* rho_red = phi + c->box.n;  // the second scratch plane
     for (long s = 0; s < n; ++s) {
         const S* src = (const S*)c->buf[c->cur];
         S* dst = (S*)c->buf[c->cur ^ 1];
         if (walls) {
-            cgm_phi_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, phi, p);
-            cgm_collide_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, dst, phi, p);
+            cgm_phi_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, phi, rho_red, p);
+            cgm_collide_kernel<S, C, true><<<grid, bx, 0, c->stream>>>(src, dst, phi, rho_red, p);
         } else {
-            cgm_phi_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, phi, p);
-            cgm_collide_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, dst, phi, p);
+            cgm_phi_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, phi, rho_red, p);
+            cgm_collide_kernel<S, C, false><<<grid, bx, 0, c->stream>>>(src, dst, phi, rho_red, p);
         }
         if (!dry) c->cur ^= 1;
     }
