@@ -75,37 +75,52 @@ __device__ __forceinline__ C cgm_ld(const S* __restrict__ src, size_t n, int pla
     return (C)Store<S>::load(src + (size_t)plane * n + cell);
 }
 
-// Pull of moving direction I: the total population f_I(x) = f*_I(x - c_I) and
-// its red part, rebuilt from the source node's red fraction and recolouring
-// vector; from behind a wall, the node's own opposite direction (half-way
-// bounce-back; the colour-gradient step has no moving lid).
+// All 19 pulled populations of a node, f_I(x) = f*_I(x - c_I), and their red
+// parts, rebuilt from the source node's red fraction and recolouring vector;
+// from behind a wall, the node's own opposite direction (half-way bounce-back;
+// the colour-gradient step has no moving lid).  Two phases: every load first
+// (totals, and a and the needed components of V at the source nodes), then
+// the red populations.
+template <typename C>
+struct RedSrc {
+    C a, vx, vy, vz;
+};
 template <typename S, typename C, bool WALLS, int I>
-__device__ __forceinline__ void cgm_pull(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
-                                         uint32_t self, C& f, C& r) {
+__device__ __forceinline__ void cgm_load(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y, int z,
+                                         uint32_t self, C& f, RedSrc<C>& g) {
     uint32_t cell;
     const bool wall = pull_source<I>(b, q, x, y, z, cell);
-    if (!WALLS || !wall) {
-        f = cgm_ld<S, C>(src, b.n, I, cell);
-        r = red_pop<C, I>(cgm_ld<S, C>(src, b.n, CGM_FRAC, cell), cgm_ld<S, C>(src, b.n, CGM_VX, cell),
-                          cgm_ld<S, C>(src, b.n, CGM_VY, cell), cgm_ld<S, C>(src, b.n, CGM_VZ, cell), f);
-    } else {
-        constexpr int J = opp_of(I);
-        f = cgm_ld<S, C>(src, b.n, J, self);
-        r = red_pop<C, J>(cgm_ld<S, C>(src, b.n, CGM_FRAC, self), cgm_ld<S, C>(src, b.n, CGM_VX, self),
-                          cgm_ld<S, C>(src, b.n, CGM_VY, self), cgm_ld<S, C>(src, b.n, CGM_VZ, self), f);
-    }
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    const bool bb = WALLS && wall;
+    const uint32_t at = bb ? self : cell;
+    f = cgm_ld<S, C>(src, b.n, bb ? opp_of(I) : I, at);
+    g.a = cgm_ld<S, C>(src, b.n, CGM_FRAC, at);
+    g.vx = cx ? cgm_ld<S, C>(src, b.n, CGM_VX, at) : (C)0;
+    g.vy = cy ? cgm_ld<S, C>(src, b.n, CGM_VY, at) : (C)0;
+    g.vz = cz ? cgm_ld<S, C>(src, b.n, CGM_VZ, at) : (C)0;
 }
-
-// All 19 pulled populations of a node and their red parts.
 template <typename S, typename C, bool WALLS>
 __device__ __forceinline__ void cgm_pull_all(const S* __restrict__ src, const Box& b, const Nbr& q, int x, int y,
                                              int z, uint32_t self, C (&f)[Q], C (&r)[Q]) {
+    RedSrc<C> g[Q];
     f[0] = cgm_ld<S, C>(src, b.n, 0, self);
     r[0] = cgm_ld<S, C>(src, b.n, CGM_RED0, self);
-#define LBM_CP(I) cgm_pull<S, C, WALLS, I>(src, b, q, x, y, z, self, f[I], r[I]);
-    LBM_CP(1) LBM_CP(2) LBM_CP(3) LBM_CP(4) LBM_CP(5) LBM_CP(6) LBM_CP(7) LBM_CP(8) LBM_CP(9) LBM_CP(10)
-    LBM_CP(11) LBM_CP(12) LBM_CP(13) LBM_CP(14) LBM_CP(15) LBM_CP(16) LBM_CP(17) LBM_CP(18)
-#undef LBM_CP
+#define LBM_CL(I) cgm_load<S, C, WALLS, I>(src, b, q, x, y, z, self, f[I], g[I]);
+    LBM_CL(1) LBM_CL(2) LBM_CL(3) LBM_CL(4) LBM_CL(5) LBM_CL(6) LBM_CL(7) LBM_CL(8) LBM_CL(9) LBM_CL(10)
+    LBM_CL(11) LBM_CL(12) LBM_CL(13) LBM_CL(14) LBM_CL(15) LBM_CL(16) LBM_CL(17) LBM_CL(18)
+#undef LBM_CL
+    // a bounce-back pull takes the opposite direction's red part at the node
+    // itself; c_opp = -c_I, so red_pop of I with -V equals red_pop of opp(I) with V
+#define LBM_CR(I)                                                                                     \
+    {                                                                                                 \
+        uint32_t cell;                                                                                \
+        const bool bb = WALLS && pull_source<I>(b, q, x, y, z, cell);                                 \
+        r[I] = bb ? red_pop<C, opp_of(I)>(g[I].a, g[I].vx, g[I].vy, g[I].vz, f[I])                   \
+                  : red_pop<C, I>(g[I].a, g[I].vx, g[I].vy, g[I].vz, f[I]);                           \
+    }
+    LBM_CR(1) LBM_CR(2) LBM_CR(3) LBM_CR(4) LBM_CR(5) LBM_CR(6) LBM_CR(7) LBM_CR(8) LBM_CR(9) LBM_CR(10)
+    LBM_CR(11) LBM_CR(12) LBM_CR(13) LBM_CR(14) LBM_CR(15) LBM_CR(16) LBM_CR(17) LBM_CR(18)
+#undef LBM_CR
 }
 
 // rho, F = rho g - rho_ref g and u = (sum f c + F/2)/rho of pulled totals
