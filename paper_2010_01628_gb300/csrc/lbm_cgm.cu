@@ -194,28 +194,45 @@ __global__ void __launch_bounds__(256) cgm_phi_kernel(const S* __restrict__ src,
     rho_red[self] = sr;
 }
 
+// grad phi = (1/c_s^2) sum_i w_i c_i phi(x + c_i): the axis and the diagonal
+// neighbours are summed apart and scaled once (3/18 and 3/36).
 template <typename C>
 __device__ __forceinline__ void grad_phi(const C* __restrict__ phi, const Box& b, const Nbr& q, int x, int y, int z,
                                          uint32_t self, C (&gr)[3]) {
-    C s[3];
-    lattice_first_moment<C>(phi, b, q, x, y, z, phi[self], s);
-    gr[0] = (C)3 * s[0];
-    gr[1] = (C)3 * s[1];
-    gr[2] = (C)3 * s[2];
+    const C own = phi[self];
+    C ax = (C)0, ay = (C)0, az = (C)0, dx = (C)0, dy = (C)0, dz = (C)0;
+#define LBM_GP(I)                                                                           \
+    {                                                                                       \
+        constexpr int ex = cx_of(I), ey = cy_of(I), ez = cz_of(I);                          \
+        constexpr bool axis = ex * ex + ey * ey + ez * ez == 1;                             \
+        const C t = field_nbr<C, I>(phi, b, q, x, y, z, own);                               \
+        if (ex) { if (axis) ax += ex > 0 ? t : -t; else dx += ex > 0 ? t : -t; }            \
+        if (ey) { if (axis) ay += ey > 0 ? t : -t; else dy += ey > 0 ? t : -t; }            \
+        if (ez) { if (axis) az += ez > 0 ? t : -t; else dz += ez > 0 ? t : -t; }            \
+    }
+    LBM_GP(1) LBM_GP(2) LBM_GP(3) LBM_GP(4) LBM_GP(5) LBM_GP(6) LBM_GP(7) LBM_GP(8) LBM_GP(9) LBM_GP(10)
+    LBM_GP(11) LBM_GP(12) LBM_GP(13) LBM_GP(14) LBM_GP(15) LBM_GP(16) LBM_GP(17) LBM_GP(18)
+#undef LBM_GP
+    const C wa = (C)(3.0 / 18.0), wd = (C)(3.0 / 36.0);
+    gr[0] = wa * ax + wd * dx;
+    gr[1] = wa * ay + wd * dy;
+    gr[2] = wa * az + wd * dz;
 }
 
 // Direction I (1..18) after the collision: adds the perturbation, stores the
 // total population and adds it and its red part to the running sums.
+// pa = (A |grad phi| w_i / |grad phi|^2, A |grad phi| B_i) for the axis (index
+// 0) and diagonal (index 1) weight classes; zero where |grad phi| vanishes.
 template <typename S, typename C, int I>
 __device__ __forceinline__ void perturb_store(S* __restrict__ dst, size_t n, uint32_t self, C fi, const C (&gr)[3],
-                                              C n2, C pert_amp, C inv_n2, C a, const C (&v)[3], C& sum_f, C& sum_r) {
+                                              const C (&pa)[2][2], C a, const C (&v)[3], C& sum_f, C& sum_r) {
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
-    constexpr int c2 = cx * cx + cy * cy + cz * cz;
-    if (n2 > (C)1e-24) {
-        const C cg = (C)cx * gr[0] + (C)cy * gr[1] + (C)cz * gr[2];
-        const C Bi = c2 == 1 ? (C)(1.0 / 18.0) : (C)(1.0 / 36.0);
-        fi += pert_amp * ((C)w_of(I) * cg * cg * inv_n2 - Bi);
-    }
+    constexpr int k = cx * cx + cy * cy + cz * cz == 1 ? 0 : 1;
+    C cg = (C)0;
+    if (cx) cg = cx > 0 ? gr[0] : -gr[0];
+    if (cy) cg = cx ? (cy > 0 ? cg + gr[1] : cg - gr[1]) : (cy > 0 ? gr[1] : -gr[1]);
+    if (cz) cg = (cx || cy) ? (cz > 0 ? cg + gr[2] : cg - gr[2]) : (cz > 0 ? gr[2] : -gr[2]);
+    fi += pa[k][0] * (cg * cg) - pa[k][1];
     Store<S>::store(dst + (size_t)I * n + self, fi);
     const C ri = red_pop<C, I>(a, v[0], v[1], v[2], fi);
     if (I == 1) {
@@ -247,17 +264,20 @@ __global__ void __launch_bounds__(256) cgm_collide_kernel(const S* __restrict__ 
     grad_phi<C>(phi, b, q, x, y, z, self, gr);
     const C n2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
     const C nrm = sqrt(n2);
-    // each colour's operator carries A_k/2 = A/2; together they perturb the total by A |grad phi| [...]
-    const C pert_amp = (C)p.A * nrm;
-    const C inv_n2 = n2 > (C)1e-24 ? (C)1 / n2 : (C)0;
-    const C inv_nrm = nrm > (C)1e-12 ? (C)1 / nrm : (C)0;
+    // each colour's operator carries A_k/2 = A/2; together they perturb the total by
+    // A |grad phi| (w_i (c_i . grad phi)^2 / |grad phi|^2 - B_i), B = 1/18, 1/36
+    const C pert_amp = n2 > (C)1e-24 ? (C)p.A * nrm : (C)0;
+    const C pq = pert_amp * (n2 > (C)1e-24 ? recip(n2) : (C)0);
+    const C pa[2][2] = {{pq * (C)(1.0 / 18.0), pert_amp * (C)(1.0 / 18.0)},
+                        {pq * (C)(1.0 / 36.0), pert_amp * (C)(1.0 / 36.0)}};
+    const C inv_nrm = nrm > (C)1e-12 ? recip(nrm) : (C)0;
     const C inv_rho = recip(s.rho);
     // recolouring: red fraction rho_r / rho, and V = beta rho_r rho_b / rho (1 - alpha) grad phi / |grad phi|
     const C a = s.rho_r * inv_rho;
     const C w = (C)p.beta * s.rho_r * s.rho_b * inv_rho * ((C)1 - s.alpha) * inv_nrm;
     const C v[3] = {w * gr[0], w * gr[1], w * gr[2]};
     C sum_f, sum_r;
-#define LBM_PS(I) perturb_store<S, C, I>(dst, b.n, self, f[I], gr, n2, pert_amp, inv_n2, a, v, sum_f, sum_r);
+#define LBM_PS(I) perturb_store<S, C, I>(dst, b.n, self, f[I], gr, pa, a, v, sum_f, sum_r);
     LBM_PS(1) LBM_PS(2) LBM_PS(3) LBM_PS(4) LBM_PS(5) LBM_PS(6) LBM_PS(7) LBM_PS(8) LBM_PS(9)
     LBM_PS(10) LBM_PS(11) LBM_PS(12) LBM_PS(13) LBM_PS(14) LBM_PS(15) LBM_PS(16) LBM_PS(17) LBM_PS(18)
 #undef LBM_PS
@@ -311,8 +331,9 @@ __global__ void cgm_init_kernel(S* __restrict__ dst, const double* __restrict__ 
     // each colour takes its density fraction of h_eq: red fraction rr / rho, V = 0
     const C a = (C)(rr / rho), zero = (C)0;
     const C v[3] = {zero, zero, zero};
+    const C pa[2][2] = {{zero, zero}, {zero, zero}};
     C sum_f, sum_r;
-#define LBM_IS(I) perturb_store<S, C, I>(dst, b.n, self, h[I], v, zero, zero, zero, a, v, sum_f, sum_r);
+#define LBM_IS(I) perturb_store<S, C, I>(dst, b.n, self, h[I], v, pa, a, v, sum_f, sum_r);
     LBM_IS(1) LBM_IS(2) LBM_IS(3) LBM_IS(4) LBM_IS(5) LBM_IS(6) LBM_IS(7) LBM_IS(8) LBM_IS(9)
     LBM_IS(10) LBM_IS(11) LBM_IS(12) LBM_IS(13) LBM_IS(14) LBM_IS(15) LBM_IS(16) LBM_IS(17) LBM_IS(18)
 #undef LBM_IS
