@@ -592,7 +592,8 @@ def run_ours(args):
                                                       "autotune_MLUPS": tuned},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": {"tma": "fluid_step_tma_kernel", "pair": "fluid_step_pair_kernel"}.get(
+                             "kernel": {"tma": "fluid_step_tma_kernel", "pair": "fluid_step_pair_kernel",
+                                        "zpair": "fluid_step_zpair_kernel"}.get(
                                  shape["variant"], "fluid_step_kernel") + f"<{prec}>",
                              "algorithmic_bytes_per_launch": algorithmic_bytes(n, prec)},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
