@@ -5,7 +5,6 @@ per-node update is shared), and FP64 domains must match the oracle; the
 autotuner must leave the state untouched; the bounded barrier wait must end
 with LBM_ERR_TIMEOUT instead of hanging.
 """
-import math
 import os
 
 import numpy as np

@@ -5,7 +5,6 @@ Tolerances: activations and kernel weights are BF16 (unit roundoff 2^-9 ~
 2e-3); four layers of rounded inputs, weights and activations put the output
 within ~1e-2 relative: forward 3e-2 and gradients 5e-2 (relative L2).
 """
-import math
 
 import numpy as np
 import pytest

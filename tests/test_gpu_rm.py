@@ -1,5 +1,4 @@
 """Raw-moment variant (App. C, N = I) on the GPU against the FP64 oracle."""
-import numpy as np
 import pytest
 
 from helpers import gpu_run, oracle_run, rel_l2

@@ -7,7 +7,6 @@ rest, and to the flow physics the variant must share with it.
 import math
 
 import numpy as np
-import pytest
 
 import oracle as O
 from paper_2010_01628_gb300 import inputs
