@@ -49,8 +49,3 @@ def gpu_run(shape, omega, steps, rho, u, phase=None, B=None, precision="fp64", p
         if ctx:
             L.lbm_destroy(ctx)
 
-
-def oracle_kwargs(kw):
-    """Translate GPU keyword arguments to the oracle's Domain keywords."""
-    out = dict(kw)
-    return out

@@ -585,3 +585,70 @@ def test_cgm_laplace_law_with_the_stated_surface_tension():
     assert abs(ratios[0] - 1) < 0.03, ratios
     assert abs(ratios[2] - 1) < 0.01, ratios
     assert abs(ratios[2] - 1) <= abs(ratios[0] - 1)
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.3])
+@pytest.mark.parametrize("axis", [0, 2])
+def test_couette_moving_lid_is_the_exact_line(tau, axis):
+    """Half-way bounce-back with the moving-wall term 2 w_i c_i.u_w / c_s^2
+    (Sec. III opening paragraph): plane Couette flow between a wall at rest
+    half a cell below y = 0 and the +y wall half a cell above y = ny - 1,
+    moving at U along x (or z), x and z periodic, no force.  The steady
+    velocity is the straight line u(y) = U (y + 1/2)/ny, with no slip at either
+    wall, for every relaxation time.  Starting from rest the oracle converges
+    onto it to round-off; a halved (or doubled) wall term moves the slope to
+    U/2 (2U), a wrong sign reverses it."""
+    ny, U = 8, 0.05
+    lid = [0.0, 0.0, 0.0]
+    lid[axis] = U
+    d = O.Domain((1, ny, 1), 1.0 / tau, periodic=(True, False, True), lid_u=tuple(lid))
+    d.init(np.ones((1, ny, 1)), np.zeros((3, 1, ny, 1)))
+    d.step(6000)
+    _, u, _, _ = d.fields()
+    y = np.arange(ny)
+    exact = U * (y + 0.5) / ny
+    np.testing.assert_allclose(u[axis, 0, :, 0], exact, rtol=0, atol=1e-12)
+    for other in {0, 1, 2} - {axis}:
+        assert np.abs(u[other]).max() < 1e-12
+
+
+@pytest.mark.parametrize("alpha,beta,rho0,steps", [(0.6, 0.12, 1.5, 8000), (0.6, 0.2, 1.0, 3000),
+                                                    (1 / 3, 0.1, 1.0, 6000)])
+def test_cgm_recolouring_sets_the_interface_width(alpha, beta, rho0, steps):
+    """The magnitude of the recolouring separation (App. E, Eqs. eq:op3r and
+    eq:op3b, with g_eq(rho, 0) = rho phi_i(alpha) and cos(theta_i) =
+    c_i.n / |c_i|) fixes the width of a flat interface at rest.
+
+    Derivation (equal colour densities, so alpha is uniform; A = 0, so the
+    total populations stay at f_eq(rho, 0) = rho phi_i(alpha)).  With the
+    interface normal along x and a = rho_r/rho, the red density after
+    streaming is Sum_i phi_i [a + beta a(1 - a) cos(theta_i)](x - c_ix).
+    Grouping directions by c_ix, with P = Sum_{c_ix = 1} phi_i = (1 - alpha)/4
+    and S = Sum_{c_ix = 1} phi_i / |c_i| = (1 - alpha)(1/12 + 1/(6 sqrt 2)),
+    a steady profile satisfies
+        P [a(x+1) + a(x-1) - 2 a(x)] = beta S [h(x+1) - h(x-1)],  h = a(1 - a).
+    Its continuum limit a' = k h, k = 2 beta S / P, is the logistic profile,
+    phi = 2a - 1 = tanh(k x / 2); the next order of the shift operators gives
+    a' = k h + (k/12) h'', so across the centre cell atanh(phi) rises by
+    (k/2)(1 - k^2/24) + O(k^5).  k is independent of alpha and of rho0.
+
+    A halved beta halves the rise; cos(theta_i) without the 1/|c_i| moves it by
+    24 %; the plain weights w_i in place of phi_i(alpha) move it by 67 % at
+    alpha = 0.6; a factor rho_r rho_b / rho instead of / rho^2 moves it by
+    50 % at rho0 = 1.5."""
+    nx = 64 if beta < 0.15 else 48
+    S = (1 - alpha) * (1.0 / 12.0 + 1.0 / (6.0 * math.sqrt(2.0)))
+    P = (1 - alpha) / 4.0
+    k = 2.0 * beta * S / P
+    d = O.Domain((nx, 1, 1), 1.0 / 0.8, physics=O.CGM, alpha_r=alpha, alpha_b=alpha, A=0.0, beta=beta)
+    x = np.arange(nx)
+    phase = np.where((x >= nx // 4) & (x < 3 * nx // 4), 1.0, -1.0).reshape(1, 1, nx)
+    d.init(rho0 * np.ones((1, 1, nx)), np.zeros((3, 1, 1, nx)), phase=phase)
+    d.step(steps)
+    _, u, ph, _ = d.fields()
+    assert np.abs(u).max() < 1e-12  # the total populations stay at rest
+    a = np.arctanh(ph.ravel())
+    c = nx // 4  # the interface sits between nodes c - 1 and c (and, mirrored, 3c - 1 and 3c)
+    predicted = 0.5 * k * (1.0 - k * k / 24.0)
+    assert abs((a[c] - a[c - 1]) / predicted - 1.0) < 3e-4
+    assert abs((a[3 * c - 1] - a[3 * c]) / predicted - 1.0) < 3e-4
