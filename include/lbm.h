@@ -320,9 +320,15 @@ lbm_status lbm_probe_fma_rate(double *fp64_fma_per_s, double *fp32_fma_per_s);
  * It allocates nothing: its scratch is a fixed 77,824-byte __device__ array
  * (1216 block partials) that every GPU loading the library holds until exit.
  * Grids beyond 2^31 - 1 nodes, or with ny or nz above 65535, are rejected with
- * LBM_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.
+ * LBM_ERR_ARG, and so are populations or out that are not device (or managed)
+ * memory of the current device (cudaPointerGetAttributes); the sizes of the
+ * two buffers cannot be checked here and are the caller's to guarantee.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset, or a context other
+ * than the device's primary one, invalidates the kept address: such callers
+ * must not use this entry point after the reset or context switch.  All calls
+ * share the array: calls that overlap on the GPU race.
  * err/err_len (optional) receive a one-line reason on failure. */
 lbm_status lbm_reduce_state_noalloc(const void *populations, lbm_precision precision, const lbm_grid *grid,
                                     const lbm_forcing *forcing, double *out, void *cuda_stream, char *err,

@@ -276,10 +276,49 @@ _lib.lbm_reduce_state_noalloc.argtypes = [_V, ctypes.c_int, ctypes.POINTER(lbm_g
 _lib.lbm_reduce_state_noalloc.restype = ctypes.c_int
 
 
+_STORED_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def _check_noalloc_tensors(populations, shape, out, precision):
+    """Argument checks of lbm_reduce_state_noalloc, all made before any device
+    work: the library writes 5 doubles through out and reads 19 planes of the
+    grid through populations, so a host tensor, a wrong dtype or a short
+    buffer would be an out-of-bounds device access."""
+    import torch
+
+    if precision not in _STORED_BYTES:
+        raise ValueError(f"unknown precision {precision!r}")
+    for name, t in (("populations", populations), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if out.dtype != torch.float64:
+        raise ValueError("out must be float64")
+    if out.numel() < 5:
+        raise ValueError("out must hold at least 5 values")
+    nx, ny, nz = (int(v) for v in shape)
+    if min(nx, ny, nz) < 1:
+        raise ValueError("grid sizes must be >= 1")
+    need = 19 * nx * ny * nz * _STORED_BYTES[precision]
+    have = populations.numel() * populations.element_size()
+    if have < need:
+        raise ValueError(f"populations hold {have} bytes, the {precision} state of {shape} needs {need}")
+    dev = torch.cuda.current_device()
+    if populations.device.index != dev or out.device.index != dev:
+        raise ValueError(f"populations and out must be on the current device cuda:{dev}")
+
+
 def lbm_reduce_state_noalloc(populations, shape, out, *, precision="fp32", periodic=(True, True, True),
                              lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), stream=None):
-    """Allocation-free reduction of a caller-owned state.  populations and out
-    are CUDA tensors (out: 5 float64).  Enqueued on the stream, not synchronised."""
+    """Allocation-free reduction of a caller-owned state.  populations: a
+    contiguous CUDA tensor holding at least 19 * nx * ny * nz stored values of
+    the precision; out: a contiguous CUDA float64 tensor of >= 5 values; both on
+    the current device (checked before the call).  Enqueued on the stream, not
+    synchronised."""
+    _check_noalloc_tensors(populations, shape, out, precision)
     gr = lbm_grid()
     gr.nx, gr.ny, gr.nz = (int(v) for v in shape)
     gr.periodic_mask = sum((1 << a) for a in range(3) if periodic[a])

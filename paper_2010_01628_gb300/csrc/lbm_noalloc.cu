@@ -154,8 +154,30 @@ extern "C" lbm_status lbm_reduce_state_noalloc(const void* populations, lbm_prec
     const double cells = (double)grid->nx * grid->ny * grid->nz;
     if (cells > 2147483647.0)
         return set_err(err, err_len, LBM_ERR_ARG, "grid exceeds the maximum of 2^31 - 1 nodes");
+    // Both buffers must be device memory of the current device: a host
+    // pointer here would become a faulting (or silently wrong) device access.
+    // The query allocates nothing.
+    int cur_dev = 0;
+    cudaError_t e = cudaGetDevice(&cur_dev);
+    if (e != cudaSuccess) return set_err(err, err_len, LBM_ERR_CUDA, "cudaGetDevice failed");
+    const void* bufs[2] = {populations, out};
+    for (int k = 0; k < 2; ++k) {
+        cudaPointerAttributes attr;
+        std::memset(&attr, 0, sizeof(attr));
+        e = cudaPointerGetAttributes(&attr, bufs[k]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // the failed query leaves a (non-sticky) error behind
+            return set_err(err, err_len, LBM_ERR_ARG,
+                           k ? "out is not a device pointer" : "populations is not a device pointer");
+        }
+        const bool on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+        if (!on_device || attr.device != cur_dev)
+            return set_err(err, err_len, LBM_ERR_ARG,
+                           k ? "out must be device memory of the current device"
+                             : "populations must be device memory of the current device");
+    }
     double* partials = nullptr;
-    cudaError_t e = partials_address(&partials);
+    e = partials_address(&partials);
     if (e != cudaSuccess) {
         char buf[256];
         std::snprintf(buf, sizeof(buf), "scratch set-up (cudaGetSymbolAddress) failed: %s", cudaGetErrorString(e));
