@@ -530,7 +530,11 @@ def lbm_cnn_set_input_raw(net, x):
     _check_cnn(_lib.lbm_cnn_set_input_raw(net, _V(x.ctypes.data), x.size), net)
 
 
-def lbm_cnn_forward(net, n_nodes):
+def lbm_cnn_forward(net, n_nodes=None):
+    """Forward pass; with n_nodes, returns the [n_nodes, 4] FP32 outputs."""
+    if n_nodes is None:
+        _check_cnn(_lib.lbm_cnn_forward(net, None, 0), net)
+        return None
     out = np.empty((n_nodes, 4), dtype=np.float32)
     _check_cnn(_lib.lbm_cnn_forward(net, _V(out.ctypes.data), out.size), net)
     return out

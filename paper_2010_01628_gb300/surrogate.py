@@ -10,7 +10,12 @@
    steady state, cosine learning-rate schedule.
 3. Evaluation: for held-out Reynolds numbers, wall time and steps to the
    residual from rest (cold) and from the network's prediction (warm;
-   inference time included).
+   inference time included).  The solver judges the network: the report
+   gives, per case, the prediction's relative L2 error against the cold run's
+   converged fields and the relative L2 difference between the warm and cold
+   runs' final fields (u, and rho - 1 against its own norm).
+4. Weights: ``save_weights``/``load_weights`` keep a trained network in an
+   ``.npz`` file (FP32 master weights plus the training recipe).
 
 Every numerical step runs in the CUDA library; this module only sequences the
 calls.  ``python -m paper_2010_01628_gb300.surrogate --n 128 ...`` runs the
@@ -92,9 +97,21 @@ def train(n, data, epochs, lr, seed=0, net=None, log=None):
     return net
 
 
-def _run(n, re, tol, check_every, max_steps, net=None):
+def _fields(ctx, n):
+    import torch
+    rho = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    u = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+    L.lbm_fields(ctx, (n, n, n), rho=rho, u=u)
+    return rho, u
+
+
+def _run(n, re, tol, check_every, max_steps, net=None, keep_fields=False):
+    """Steps, residual and wall seconds to the steady residual from rest
+    (net None) or from the network's prediction (inference inside the timed
+    region); with keep_fields, also the final (rho, u) on the GPU."""
     import torch
     ctx = _cavity(n, re)
+    fields = None
     try:
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -102,26 +119,88 @@ def _run(n, re, tol, check_every, max_steps, net=None):
             L.lbm_cnn_warm_start(net, ctx, re)
         steps, res = L.lbm_run_to_steady(ctx, max_steps, check_every, tol)
         dt = time.perf_counter() - t
+        if keep_fields:
+            fields = _fields(ctx, n)
     finally:
         L.lbm_destroy(ctx)
-    return steps, res, dt
+    return steps, res, dt, fields
 
 
-def evaluate(net, n, re_list, tol=1e-6, check_every=100, max_steps=400_000, log=None):
+def prediction(net, n, re):
+    """The network's (rho, u) for `re` as the solver sees it: a context
+    initialised by lbm_cnn_warm_start, read back before any step."""
+    ctx = _cavity(n, re)
+    try:
+        L.lbm_cnn_warm_start(net, ctx, re)
+        return _fields(ctx, n)
+    finally:
+        L.lbm_destroy(ctx)
+
+
+def _rel(a, b, ref):
+    import torch
+    d = float(torch.linalg.vector_norm(a - b))
+    r = float(torch.linalg.vector_norm(ref))
+    return d / r if r > 0 else d
+
+
+def judge(pred, cold, warm):
+    """Relative L2 errors: the prediction against the cold run's converged
+    fields, and the warm run's final fields against the cold run's (u against
+    ||u_cold||, rho against ||rho_cold - 1||)."""
+    (rp, up), (rc, uc), (rw, uw) = pred, cold, warm
+    drc = rc - 1.0
+    return {"net_err_u": _rel(up, uc, uc), "net_err_rho": _rel(rp, rc, drc),
+            "warm_vs_cold_u": _rel(uw, uc, uc), "warm_vs_cold_rho": _rel(rw, rc, drc)}
+
+
+def evaluate(net, n, re_list, tol=1e-6, check_every=100, max_steps=400_000, log=None, judged=True):
     cases = []
     for re in re_list:
-        cs, cr, ct = _run(n, float(re), tol, check_every, max_steps)
-        ws, wr, wt = _run(n, float(re), tol, check_every, max_steps, net)
-        cases.append({"re": float(re), "cold_steps": cs, "cold_seconds": ct, "cold_residual": cr, "warm_steps": ws,
-                      "warm_seconds": wt, "warm_residual": wr})
+        re = float(re)
+        cs, cr, ct, cf = _run(n, re, tol, check_every, max_steps, keep_fields=judged)
+        ws, wr, wt, wf = _run(n, re, tol, check_every, max_steps, net, keep_fields=judged)
+        case = {"re": re, "cold_steps": cs, "cold_seconds": ct, "cold_residual": cr, "warm_steps": ws,
+                "warm_seconds": wt, "warm_residual": wr}
+        if judged:
+            case.update(judge(prediction(net, n, re), cf, wf))
+            del cf, wf
+        cases.append(case)
         if log:
-            log(f"Re={re:7.1f} cold {cs} steps {ct:.2f}s | warm {ws} steps {wt:.2f}s")
+            extra = (f" | net err u {case['net_err_u']:.2e} warm-cold u {case['warm_vs_cold_u']:.2e}"
+                     if judged else "")
+            log(f"Re={re:7.1f} cold {cs} steps {ct:.2f}s | warm {ws} steps {wt:.2f}s{extra}")
     cold = [c["cold_seconds"] for c in cases]
     warm = [c["warm_seconds"] for c in cases]
-    return {"cases": cases, "cold_mean_s": statistics.mean(cold), "warm_mean_s": statistics.mean(warm),
-            "cold_median_s": statistics.median(cold), "warm_median_s": statistics.median(warm),
-            "mean_time_reduction": 1.0 - statistics.mean(warm) / statistics.mean(cold),
-            "median_time_reduction": 1.0 - statistics.median(warm) / statistics.median(cold)}
+    rep = {"cases": cases, "cold_mean_s": statistics.mean(cold), "warm_mean_s": statistics.mean(warm),
+           "cold_median_s": statistics.median(cold), "warm_median_s": statistics.median(warm),
+           "mean_time_reduction": 1.0 - statistics.mean(warm) / statistics.mean(cold),
+           "median_time_reduction": 1.0 - statistics.median(warm) / statistics.median(cold),
+           "cold_mean_steps": statistics.mean(c["cold_steps"] for c in cases),
+           "warm_mean_steps": statistics.mean(c["warm_steps"] for c in cases)}
+    if judged:
+        for k in ("net_err_u", "net_err_rho", "warm_vs_cold_u", "warm_vs_cold_rho"):
+            rep[k + "_max"] = max(c[k] for c in cases)
+            rep[k + "_median"] = statistics.median(c[k] for c in cases)
+    return rep
+
+
+def save_weights(net, path, **meta):
+    """Write the network's FP32 master weights and `meta` (the training
+    recipe) to an .npz file."""
+    w = L.lbm_cnn_get_weights(net)
+    np.savez_compressed(path, weights=w, meta=json.dumps(meta))
+
+
+def load_weights(path):
+    """(FP32 weights, meta dict) from an .npz file written by save_weights;
+    the parameter count must match the library's network."""
+    with np.load(path) as z:
+        w = np.ascontiguousarray(z["weights"], dtype=np.float32)
+        meta = json.loads(str(z["meta"]))
+    if w.size != L.lbm_cnn_param_count():
+        raise ValueError(f"{path}: {w.size} parameters, the network has {L.lbm_cnn_param_count()}")
+    return w, meta
 
 
 def main():
@@ -135,6 +214,7 @@ def main():
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--max-steps", type=int, default=400_000)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save-weights", default=None, help="write the trained network to this .npz file")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -152,6 +232,10 @@ def main():
     net = train(args.n, data, args.epochs, args.lr, log=log)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    if args.save_weights:
+        save_weights(net, args.save_weights, grid=args.n, train_states=len(data), epochs=args.epochs, lr=args.lr,
+                     tol=args.tol, check_every=args.check_every, reynolds_seed=4, train_count=args.train,
+                     heldout_count=args.heldout)
     rep = evaluate(net, args.n, held_re, args.tol, args.check_every, max_steps=args.max_steps, log=log)
     L.lbm_cnn_destroy(net)
     rep.update({"grid": args.n, "train_states": len(data), "heldout": len(held_re), "epochs": args.epochs,

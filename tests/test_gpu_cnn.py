@@ -1,5 +1,10 @@
-"""Warm-start network on the GPU (BF16 tensor-core kernels) against the FP64
-numpy oracle, and the warm start's gain over a cold start.
+"""Warm-start network on the GPU (tcgen05 BF16 tensor-core kernels with TMEM
+accumulators and tensor-map TMA staging) against the FP64 numpy oracle, and
+the warm start's gain over a cold start.
+
+Shapes cover the tile boxes the kernels choose: 16 x 8 x 1 and 8 x 8 x 2 boxes
+on small ragged grids, and 128-voxel x-rows with a ragged second tile
+(nx = 130), where more CTAs than tiles leave some weight-gradient CTAs empty.
 
 Tolerances: activations and kernel weights are BF16 (unit roundoff 2^-9 ~
 2e-3); four layers of rounded inputs, weights and activations put the output
@@ -25,7 +30,7 @@ def test_param_layout_matches_oracle():
     assert L.lbm_cnn_param_count() == C.param_count()
 
 
-@pytest.mark.parametrize("shape", [(13, 9, 11), (16, 16, 16)])
+@pytest.mark.parametrize("shape", [(13, 9, 11), (16, 16, 16), (130, 5, 4)])
 def test_forward_matches_oracle(shape):
     from paper_2010_01628_gb300 import binding as L
     nx, ny, nz = shape
@@ -55,9 +60,9 @@ def test_features_and_forward_for_reynolds():
     assert rel_l2(got, ref) < 3e-2
 
 
-def test_gradient_matches_oracle():
+@pytest.mark.parametrize("shape", [(10, 12, 9), (130, 4, 3)])
+def test_gradient_matches_oracle(shape):
     from paper_2010_01628_gb300 import binding as L
-    shape = (10, 12, 9)
     nx, ny, nz = shape
     p = params(4)
     rng = np.random.default_rng(5)
@@ -105,7 +110,15 @@ def test_adam_step_on_own_gradient():
 def test_warm_start_reaches_steady_state_sooner():
     """Train on a few solver steady states of a small cavity, then compare the
     steps to a 1e-6 residual from rest and from the network's prediction for
-    held-out Reynolds numbers."""
+    held-out Reynolds numbers, and let the solver judge the network.
+
+    The residual is the mean per-step change over the check interval, so a run
+    stops at a distance of about r / lambda from the fixed point (lambda the
+    slowest decay rate per step, ~1e-3 on this cavity): the warm and cold runs
+    end on the same steady state only to that distance, ~1e-3 relative in u.
+    Bounds: warm vs cold final u within 2e-2 (measured 4e-3) and rho - 1
+    within 5e-2 of its norm (measured 1e-2); the prediction closer to the
+    converged u than the rest state is (relative error < 0.5; rest = 1)."""
     from paper_2010_01628_gb300 import surrogate as S
     n = 24
     train_re = np.linspace(100, 300, 8)
@@ -119,3 +132,6 @@ def test_warm_start_reaches_steady_state_sooner():
         L.lbm_cnn_destroy(net)
     for r in rep["cases"]:
         assert r["warm_steps"] < r["cold_steps"], r
+        assert r["warm_vs_cold_u"] < 2e-2, r
+        assert r["warm_vs_cold_rho"] < 5e-2, r
+        assert r["net_err_u"] < 0.5, r
