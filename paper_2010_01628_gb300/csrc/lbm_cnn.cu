@@ -9,17 +9,19 @@
 // to multiples of 16); master weights, gradients and Adam moments are FP32.
 //
 // Kernels:
-//  - conv_mma: implicit GEMM on the tensor cores (mma.sync m16n8k16 BF16 with
-//    FP32 accumulation).  A warp computes 64 voxels x all output channels;
-//    the 27 taps x input channels form the reduction.  The same kernel runs the
-//    backward data pass with the flipped, transposed weights.
-//  - conv_wgrad: weight and bias gradients, FP32 reductions over voxel chunks
-//    (one partial per CTA, summed in a fixed order).
+//  - conv_tc: implicit GEMM on the tensor cores: tcgen05.mma (BF16 operands,
+//    FP32 accumulators in TMEM) fed by tensor-map TMA copies of the 27 shifted
+//    128-voxel boxes; the same kernel runs the backward data pass with the
+//    flipped, transposed weights.
+//  - wgrad_tc: weight gradients on the tensor cores (taps x input channels as
+//    M, output channels as N, voxels as K), one partial per CTA summed in a
+//    fixed order; bias_grad: bias gradients.
 //  - adam: the optimiser step on the FP32 master weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,6 +29,7 @@
 #include <vector>
 
 #include "lbm_internal.h"
+#include "lbm_tc.cuh"
 
 namespace cnn {
 
@@ -37,7 +40,6 @@ constexpr int CH[NL + 1] = {16, 32, 32, 32, 16};
 constexpr int CH_REAL[NL + 1] = {5, 32, 32, 32, 4};
 constexpr float RHO_SCALE = 30.f;  // network output 0 = (rho - 1) * RHO_SCALE
 constexpr float U_SCALE = 10.f;    // outputs 1..3 = u * U_SCALE (lid speed 0.1 -> 1)
-constexpr int WG_BLOCKS = 304;     // CTAs of the weight-gradient reduction
 
 constexpr int layer_params(int l) { return 27 * CH_REAL[l + 1] * CH_REAL[l] + CH_REAL[l + 1]; }
 constexpr int total_params() { return layer_params(0) + layer_params(1) + layer_params(2) + layer_params(3); }
@@ -60,171 +62,483 @@ __device__ __forceinline__ uint32_t bf_pack(float a, float b) {
            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// ---------------------------------------------------------------------------
+// Tensor-core convolution (tcgen05, TMEM accumulators, TMA operand staging).
+//
+// Implicit GEMM per tile of 128 voxels: D[voxel][co] = sum over the 27 taps of
+// A_tap[voxel][ci] W[tap][co][ci].  A tile is a box of BX x BY x BZ = 128
+// voxels; A_tap is the same box shifted by the tap's offset, loaded by a 4D
+// tensor-map copy whose out-of-range elements are zero (the convolution's zero
+// padding).  Rows of A and W are K-major (channels contiguous) in the TMA's
+// 64-byte (CI = 32) or 32-byte (CI = 16) swizzle.  The 27 weight taps stay in
+// shared memory for the CTA's life.
+//
+// Roles (192 threads): warp 0 lane 0 issues the TMA copies into a ring of
+// NSTAGE A buffers; warp 1 allocates TMEM and its lane 0 issues the MMAs
+// (M = 128, N = CO, K = 16) into one of two TMEM accumulators; warps 2-5 read
+// the finished accumulator (each warp its 32-lane quarter: one voxel per
+// thread, CO columns), apply the epilogue and store.  Every wait is bounded
+// (TC_WAIT_NS); on expiry the kernel records LBM_ERR_TIMEOUT in *status, the
+// other roles stop, the copies and MMAs in flight are drained (bounded) and
+// TMEM is freed.
+constexpr int TILE_M = 128;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;
+
+struct TileGeom {
+    int nx, ny, nz;     // grid
+    int bx, by, bz;     // box of one tile (bx * by * bz = 128)
+    int ntx, nty, ntz;  // tiles per axis
+    int ntiles;
+};
+
+__device__ __forceinline__ void tile_origin(const TileGeom& g, int t, int& x0, int& y0, int& z0) {
+    x0 = (t % g.ntx) * g.bx;
+    y0 = ((t / g.ntx) % g.nty) * g.by;
+    z0 = (t / (g.ntx * g.nty)) * g.bz;
 }
 
-// EPI: 0 = +bias, ReLU, BF16 out; 1 = +bias, FP32 out; 2 = ReLU mask from
-// `gate` (the forward activation of this layer's output), BF16 out, no bias.
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+    const uint32_t a = lbm::smem_u32(p);
+    return p + (((a + 1023u) & ~1023u) - a);
+}
+
+// Wait for phase `parity` of `bar`, giving up when another role aborted or the
+// deadline passed (then recording the timeout).
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+    if (lbm::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = lbm::global_ns();
+    while (!lbm::mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (lbm::global_ns() - t0 > TC_WAIT_NS) {
+            *abort_flag = 1;
+            atomicExch(status, (int)LBM_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+// Bounded wait that ignores the abort flag (draining before exit).
+__device__ __forceinline__ void tc_drain(uint64_t* bar, uint32_t parity) {
+    lbm::mbar_wait_bounded(bar, parity, TC_WAIT_NS);
+}
+
+template <int CI, int CO, int NSTAGE>
+struct ConvLayout {
+    static constexpr int A_BYTES = TILE_M * CI * 2;
+    static constexpr int W_BYTES = 27 * CO * CI * 2;
+    static constexpr int A_OFF = (W_BYTES + 1023) / 1024 * 1024;
+    static constexpr int BAR_OFF = A_OFF + NSTAGE * A_BYTES;
+    static constexpr int NBAR = 2 * NSTAGE + 6;  // full, empty, tmem full x2, tmem empty x2, weights, drain
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 1024;  // + TMEM slot, abort flag, alignment slack
+    static constexpr uint32_t SWZ = CI == 32 ? tc::SW_64B : tc::SW_32B;
+    static constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_M, CO, false, false);
+    static_assert(A_BYTES % 1024 == 0, "A stages must keep the swizzle alignment");
+};
+
+constexpr int CONV_STAGES = 6;
+
+// EPI: 0 = +bias, ReLU, BF16 out [P][CO]; 1 = +bias, FP32 out [P][CO];
+// 2 = zero where `gate` (this layer's forward activation) is not positive,
+// BF16 out, no bias.
 template <int CI, int CO, int EPI>
-__global__ void __launch_bounds__(128) conv_mma(const __nv_bfloat16* __restrict__ X,
-                                                const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
-                                                void* __restrict__ Y, const __nv_bfloat16* __restrict__ gate,
-                                                Shape s) {
-    extern __shared__ __align__(16) uint32_t wsm[];  // [27][CO][CI/2] packed bf16 pairs
-    constexpr int NT = CO / 8, KS = CI / 16;
-    for (int i = threadIdx.x; i < 27 * CO * CI / 2; i += blockDim.x) wsm[i] = reinterpret_cast<const uint32_t*>(Wt)[i];
+__global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorMap mapX,
+                                               const __grid_constant__ CUtensorMap mapW, const float* __restrict__ bias,
+                                               void* __restrict__ Y, const __nv_bfloat16* __restrict__ gate,
+                                               TileGeom g, int* status) {
+    using Lay = ConvLayout<CI, CO, CONV_STAGES>;
+    constexpr int NSTAGE = CONV_STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sW = sm;
+    uint8_t* sA = sm + Lay::A_OFF;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + Lay::BAR_OFF);
+    uint64_t* empty = full + NSTAGE;
+    uint64_t* tfull = empty + NSTAGE;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wfull = tempty + 2;
+    uint64_t* drain = wfull + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            lbm::mbar_init(&full[s], 1);
+            lbm::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            lbm::mbar_init(&tfull[a], 1);
+            lbm::mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+        }
+        lbm::mbar_init(wfull, 1);
+        lbm::mbar_init(drain, 1);
+        *abort_flag = 0;
+        lbm::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, 64);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long base = ((long)blockIdx.x * 4 + warp) * 64;
-    const int r = lane >> 2, q = lane & 3;
-    const uint32_t* X32 = reinterpret_cast<const uint32_t*>(X);
-    // the 8 voxels this thread loads A rows for: rows r and r+8 of 4 m-tiles
-    int vx[8], vy[8], vz[8];
-    bool vin[8];
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (threadIdx.x == 0) {
+        // ---- TMA producer ----
+        tc::prefetch_map(&mapX);
+        tc::prefetch_map(&mapW);
+        lbm::mbar_arrive_expect_tx(wfull, Lay::W_BYTES);
+        tc::tma_load_3d(sW, &mapW, 0, 0, 0, wfull);
+        int armed[NSTAGE];
+        for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < g.ntiles && ok; t += gridDim.x) {
+            int x0, y0, z0;
+            tile_origin(g, t, x0, y0, z0);
+            for (int tap = 0; tap < 27; ++tap) {
+                if (!tc_wait(&empty[stage], phase ^ 1u, abort_flag, status)) {
+                    ok = false;
+                    break;
+                }
+                int dx, dy, dz;
+                tap_offset(tap, dx, dy, dz);
+                lbm::mbar_arrive_expect_tx(&full[stage], Lay::A_BYTES);
+                tc::tma_load_4d(sA + stage * Lay::A_BYTES, &mapX, 0, x0 + dx, y0 + dy, z0 + dz, &full[stage]);
+                armed[stage] = (int)phase;
+                if (++stage == NSTAGE) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        // the copies land by themselves: wait for the last one of every stage
+        for (int s = 0; s < NSTAGE; ++s)
+            if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
+        tc_drain(wfull, 0);
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer ----
+        if (tc_wait(wfull, 0, abort_flag, status)) {
+            tc::fence_after_sync();
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool ok = true;
+            const uint32_t a0 = lbm::smem_u32(sA), w0 = lbm::smem_u32(sW);
+            for (int t = blockIdx.x; t < g.ntiles && ok; t += gridDim.x, ++it) {
+                const int acc = it & 1;
+                if (!tc_wait(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, abort_flag, status)) break;
+                tc::fence_after_sync();
+                const uint32_t d = tbase + (uint32_t)(acc * CO);
+                for (int tap = 0; tap < 27; ++tap) {
+                    if (!tc_wait(&full[stage], phase, abort_flag, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const long p = base + (j >> 1) * 16 + r + (j & 1) * 8;
-        vin[j] = p < s.P;
-        const long pp = vin[j] ? p : 0;
-        vx[j] = (int)(pp % s.nx);
-        vy[j] = (int)((pp / s.nx) % s.ny);
-        vz[j] = (int)(pp / ((long)s.nx * s.ny));
+                    for (int k = 0; k < CI / 16; ++k) {
+                        const uint64_t ad = tc::smem_desc(a0 + stage * Lay::A_BYTES + k * 32, 16, 8 * CI * 2, Lay::SWZ);
+                        const uint64_t bd = tc::smem_desc(w0 + tap * CO * CI * 2 + k * 32, 16, 8 * CI * 2, Lay::SWZ);
+                        tc::mma_bf16(d, ad, bd, Lay::IDESC, tap > 0 || k > 0);
+                    }
+                    tc::mma_commit(&empty[stage]);
+                    if (++stage == NSTAGE) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (ok) tc::mma_commit(&tfull[acc]);
+            }
+        }
+        tc::mma_commit(drain);
+        tc_drain(drain, 0);
+    } else if (warp >= 2) {
+        // ---- epilogue: TMEM -> registers -> global ----
+        const int q = warp & 3;  // TMEM lanes 32q .. 32q + 31
+        const int row = q * 32 + lane;
+        float bvals[CO];
+#pragma unroll
+        for (int co = 0; co < CO; ++co) bvals[co] = (EPI == 2) ? 0.f : __ldg(bias + co);
+        int it = 0;
+        for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x, ++it) {
+            const int acc = it & 1;
+            bool ok = false;
+            if (lane == 0) ok = tc_wait(&tfull[acc], ((uint32_t)it >> 1) & 1u, abort_flag, status);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc::fence_after_sync();
+            uint32_t r[CO];
+            if constexpr (CO == 32)
+                tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CO), r);
+            else
+                tc::tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CO), r);
+            tc::tmem_ld_wait();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+            int x0, y0, z0;
+            tile_origin(g, t, x0, y0, z0);
+            const int x = x0 + row % g.bx, y = y0 + (row / g.bx) % g.by, z = z0 + row / (g.bx * g.by);
+            if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+            const long p = ((long)z * g.ny + y) * g.nx + x;
+            float v[CO];
+#pragma unroll
+            for (int co = 0; co < CO; ++co) v[co] = __uint_as_float(r[co]) + bvals[co];
+            if (EPI == 0) {
+#pragma unroll
+                for (int co = 0; co < CO; ++co) v[co] = fmaxf(v[co], 0.f);
+            }
+            if (EPI == 2) {
+                const uint4* gp = reinterpret_cast<const uint4*>(gate) + p * (CO / 8);
+#pragma unroll
+                for (int j = 0; j < CO / 8; ++j) {
+                    const uint4 gw = __ldg(gp + j);
+                    const uint32_t w4[4] = {gw.x, gw.y, gw.z, gw.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        if (!(bf_lo(w4[h]) > 0.f)) v[8 * j + 2 * h] = 0.f;
+                        if (!(bf_hi(w4[h]) > 0.f)) v[8 * j + 2 * h + 1] = 0.f;
+                    }
+                }
+            }
+            if (EPI == 1) {
+                float4* yp = reinterpret_cast<float4*>(Y) + p * (CO / 4);
+#pragma unroll
+                for (int j = 0; j < CO / 4; ++j) yp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            } else {
+                uint4* yp = reinterpret_cast<uint4*>(Y) + p * (CO / 8);
+#pragma unroll
+                for (int j = 0; j < CO / 8; ++j)
+                    yp[j] = make_uint4(bf_pack(v[8 * j], v[8 * j + 1]), bf_pack(v[8 * j + 2], v[8 * j + 3]),
+                                       bf_pack(v[8 * j + 4], v[8 * j + 5]), bf_pack(v[8 * j + 6], v[8 * j + 7]));
+            }
+        }
     }
-    float acc[4][NT][4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int n = 0; n < NT; ++n)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[m][n][k] = 0.f;
-    for (int tap = 0; tap < 27; ++tap) {
-        int dx, dy, dz;
-        tap_offset(tap, dx, dy, dz);
-        long src[8];
-        bool ok[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int x = vx[j] + dx, y = vy[j] + dy, z = vz[j] + dz;
-            ok[j] = vin[j] && x >= 0 && x < s.nx && y >= 0 && y < s.ny && z >= 0 && z < s.nz;
-            src[j] = ok[j] ? (((long)z * s.ny + y) * s.nx + x) * (CI / 2) : 0;
-        }
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            const int k0 = ks * 8 + q;  // packed-pair index of channels 2q, 2q+1 within this k-step
-            uint32_t a[4][4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                a[m][0] = ok[2 * m] ? __ldg(X32 + src[2 * m] + k0) : 0u;
-                a[m][1] = ok[2 * m + 1] ? __ldg(X32 + src[2 * m + 1] + k0) : 0u;
-                a[m][2] = ok[2 * m] ? __ldg(X32 + src[2 * m] + k0 + 4) : 0u;
-                a[m][3] = ok[2 * m + 1] ? __ldg(X32 + src[2 * m + 1] + k0 + 4) : 0u;
-            }
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const uint32_t* wrow = wsm + ((size_t)tap * CO + n * 8 + r) * (CI / 2) + k0;
-                const uint32_t b0 = wrow[0], b1 = wrow[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) mma_bf16(acc[m][n], a[m], b0, b1);
-            }
-        }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, 64);
     }
-    // epilogue: D rows r (c0, c1) and r + 8 (c2, c3), columns n*8 + 2q, +1
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long p = base + m * 16 + r + h * 8;
-            if (p >= s.P) continue;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int co = n * 8 + 2 * q;
-                float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
-                if (EPI == 0 || EPI == 1) {
-                    v0 += bias[co];
-                    v1 += bias[co + 1];
-                }
-                if (EPI == 0) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                if (EPI == 2) {
-                    const uint32_t g = reinterpret_cast<const uint32_t*>(gate)[p * (CO / 2) + co / 2];
-                    if (!(bf_lo(g) > 0.f)) v0 = 0.f;
-                    if (!(bf_hi(g) > 0.f)) v1 = 0.f;
-                }
-                if (EPI == 1) {
-                    float* Yf = reinterpret_cast<float*>(Y);
-                    Yf[p * CO + co] = v0;
-                    Yf[p * CO + co + 1] = v1;
-                } else {
-                    reinterpret_cast<uint32_t*>(Y)[p * (CO / 2) + co / 2] = bf_pack(v0, v1);
-                }
-            }
-        }
 }
 
-// Weight/bias gradients: dW[tap][co][ci] = sum_p dY[p][co] X[p + off(tap)][ci],
-// db[co] = sum_p dY[p][co].  256 threads: thread (co = t % 32, group g = t / 32)
-// accumulates taps g, g+8, g+16, g+24 for all CI; one partial per CTA.
+// Weight gradient on the tensor cores: dW[tap][co][ci] = sum_p dY[p][co]
+// X[p + off(tap)][ci], as D[(tap, ci)][co] = A[(tap, ci)][p] B[p][co] with
+// M = 128 = TG taps x CI channels per tap group (TG = 4 for CI = 32, 8 for
+// CI = 16; 7 or 4 groups, the last padded with a repeated tap whose rows are
+// discarded) and the voxels of a tile as K.  Both operands are MN-major (the
+// channels are contiguous in the staged boxes): the TG shifted X boxes of a
+// group sit back to back, so one descriptor spans them with the box size as
+// its leading (M) offset.  Every group accumulates in its own TMEM columns
+// over all tiles of the CTA's contiguous range; the epilogue writes one
+// partial per CTA, laid out [27][CO][CI], summed later in a fixed order.
 template <int CI, int CO>
-__global__ void __launch_bounds__(256) conv_wgrad(const __nv_bfloat16* __restrict__ X,
-                                                  const __nv_bfloat16* __restrict__ dY, float* __restrict__ partial,
-                                                  Shape s) {
-    const int co = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const bool co_ok = co < CO;
-    float acc[4][CI];
-    float db = 0.f;
+struct WgLayout {
+    static constexpr int TG = TILE_M / CI;
+    static constexpr int NG = (27 + TG - 1) / TG;
+    static constexpr int XB = TILE_M * CI * 2;
+    static constexpr int STAGE = TG * XB;
+    static constexpr int YB = TILE_M * CO * 2;
+    static constexpr int NSTAGE = 4;
+    static constexpr int Y_OFF = NSTAGE * STAGE;
+    static constexpr int BAR_OFF = Y_OFF + 2 * YB;
+    static constexpr int NBAR = 2 * NSTAGE + 4 + 2;  // full, empty, y full x2, y empty x2, acc full, drain
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 1024;
+    static constexpr int TCOLS_USED = NG * CO;
+    static constexpr uint32_t TCOLS = TCOLS_USED <= 32 ? 32 : (TCOLS_USED <= 64 ? 64 : (TCOLS_USED <= 128 ? 128 : 256));
+    static constexpr uint32_t SWX = CI == 32 ? tc::SW_64B : tc::SW_32B;
+    static constexpr uint32_t SWY = CO == 32 ? tc::SW_64B : tc::SW_32B;
+    static constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_M, CO, true, true);
+    static_assert(TG * CI == TILE_M && TCOLS_USED <= 256, "tap groups must fill M = 128 within 256 TMEM columns");
+    static_assert(XB % 1024 == 0 && YB % 1024 == 0, "boxes must keep the swizzle alignment");
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(192) wgrad_tc(const __grid_constant__ CUtensorMap mapX,
+                                                const __grid_constant__ CUtensorMap mapY, float* __restrict__ partial,
+                                                TileGeom g, int* status) {
+    using Lay = WgLayout<CI, CO>;
+    constexpr int NSTAGE = Lay::NSTAGE;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = align1024(smem_raw);
+    uint8_t* sA = sm;
+    uint8_t* sY = sm + Lay::Y_OFF;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + Lay::BAR_OFF);
+    uint64_t* empty = full + NSTAGE;
+    uint64_t* yfull = empty + NSTAGE;
+    uint64_t* yempty = yfull + 2;
+    uint64_t* accfull = yempty + 2;
+    uint64_t* drain = accfull + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per = (g.ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t_begin = min(g.ntiles, (int)blockIdx.x * per), t_end = min(g.ntiles, t_begin + per);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            lbm::mbar_init(&full[s], 1);
+            lbm::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            lbm::mbar_init(&yfull[a], 1);
+            lbm::mbar_init(&yempty[a], 1);
+        }
+        lbm::mbar_init(accfull, 1);
+        lbm::mbar_init(drain, 1);
+        *abort_flag = 0;
+        lbm::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tslot, Lay::TCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (threadIdx.x == 0) {
+        // ---- TMA producer ----
+        tc::prefetch_map(&mapX);
+        tc::prefetch_map(&mapY);
+        int armed[NSTAGE], yarmed[2] = {-1, -1};
+        for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int t = t_begin, it = 0; t < t_end && ok; ++t, ++it) {
+            int x0, y0, z0;
+            tile_origin(g, t, x0, y0, z0);
+            const int ys = it & 1;
+            if (!tc_wait(&yempty[ys], (((uint32_t)it >> 1) & 1u) ^ 1u, abort_flag, status)) break;
+            lbm::mbar_arrive_expect_tx(&yfull[ys], Lay::YB);
+            tc::tma_load_4d(sY + ys * Lay::YB, &mapY, 0, x0, y0, z0, &yfull[ys]);
+            yarmed[ys] = (int)(((uint32_t)it >> 1) & 1u);
+            for (int gi = 0; gi < Lay::NG; ++gi) {
+                if (!tc_wait(&empty[stage], phase ^ 1u, abort_flag, status)) {
+                    ok = false;
+                    break;
+                }
+                lbm::mbar_arrive_expect_tx(&full[stage], Lay::STAGE);
+                for (int j = 0; j < Lay::TG; ++j) {
+                    const int tap = min(26, gi * Lay::TG + j);
+                    int dx, dy, dz;
+                    tap_offset(tap, dx, dy, dz);
+                    tc::tma_load_4d(sA + stage * Lay::STAGE + j * Lay::XB, &mapX, 0, x0 + dx, y0 + dy, z0 + dz,
+                                    &full[stage]);
+                }
+                armed[stage] = (int)phase;
+                if (++stage == NSTAGE) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        for (int s = 0; s < NSTAGE; ++s)
+            if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
+        for (int s = 0; s < 2; ++s)
+            if (yarmed[s] >= 0) tc_drain(&yfull[s], (uint32_t)yarmed[s]);
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer ----
+        const uint32_t a0 = lbm::smem_u32(sA), y0s = lbm::smem_u32(sY);
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int t = t_begin, it = 0; t < t_end && ok; ++t, ++it) {
+            const int ys = it & 1;
+            if (!tc_wait(&yfull[ys], ((uint32_t)it >> 1) & 1u, abort_flag, status)) {
+                ok = false;
+                break;
+            }
+            for (int gi = 0; gi < Lay::NG; ++gi) {
+                if (!tc_wait(&full[stage], phase, abort_flag, status)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+                for (int k = 0; k < TILE_M / 16; ++k) {
+                    const uint64_t ad =
+                        tc::smem_desc(a0 + stage * Lay::STAGE + k * 16 * CI * 2, Lay::XB, 8 * CI * 2, Lay::SWX);
+                    const uint64_t bd = tc::smem_desc(y0s + ys * Lay::YB + k * 16 * CO * 2, Lay::YB, 8 * CO * 2, Lay::SWY);
+                    tc::mma_bf16(tbase + (uint32_t)(gi * CO), ad, bd, Lay::IDESC, it > 0 || k > 0);
+                }
+                tc::mma_commit(&empty[stage]);
+                if (++stage == NSTAGE) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+            if (ok) tc::mma_commit(&yempty[ys]);
+        }
+        if (ok) tc::mma_commit(accfull);
+        tc::mma_commit(drain);
+        tc_drain(drain, 0);
+    } else if (warp >= 2) {
+        // ---- epilogue: accumulated groups -> this CTA's partial ----
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        const int tsub = m / CI, ci = m % CI;
+        float* out = partial + (size_t)blockIdx.x * (27 * CO * CI + CO);
+        const bool have = t_end > t_begin;
+        bool ok = true;
+        if (have) {
+            if (lane == 0) ok = tc_wait(accfull, 0, abort_flag, status);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok) tc::fence_after_sync();
+        }
+        if (ok) {
+            for (int gi = 0; gi < Lay::NG; ++gi) {
+                uint32_t r[CO];
+                if (have) {
+                    if constexpr (CO == 32)
+                        tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(gi * CO), r);
+                    else
+                        tc::tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(gi * CO), r);
+                    tc::tmem_ld_wait();
+                } else {
 #pragma unroll
-        for (int c = 0; c < CI; ++c) acc[t][c] = 0.f;
-    const long chunk = (s.P + gridDim.x - 1) / gridDim.x;
-    const long p0 = blockIdx.x * chunk, p1 = min(s.P, p0 + chunk);
-    const unsigned short* dYs = reinterpret_cast<const unsigned short*>(dY);
-    const uint4* X4 = reinterpret_cast<const uint4*>(X);
-    for (long p = p0; p < p1; ++p) {
-        const float gy = co_ok ? __uint_as_float((uint32_t)__ldg(dYs + p * CO + co) << 16) : 0.f;
-        db += gy;
-        const int x = (int)(p % s.nx), y = (int)((p / s.nx) % s.ny), z = (int)(p / ((long)s.nx * s.ny));
+                    for (int co = 0; co < CO; ++co) r[co] = 0u;
+                }
+                const int tap = gi * Lay::TG + tsub;
+                if (tap < 27) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int tap = g + 8 * t;
-            if (tap >= 27) continue;
-            int dx, dy, dz;
-            tap_offset(tap, dx, dy, dz);
-            const int xs = x + dx, ys = y + dy, zs = z + dz;
-            if (xs < 0 || xs >= s.nx || ys < 0 || ys >= s.ny || zs < 0 || zs >= s.nz) continue;
-            const long q = ((long)zs * s.ny + ys) * s.nx + xs;
-#pragma unroll
-            for (int v = 0; v < CI / 8; ++v) {
-                const uint4 w = __ldg(X4 + q * (CI / 8) + v);
-                acc[t][8 * v + 0] += gy * bf_lo(w.x);
-                acc[t][8 * v + 1] += gy * bf_hi(w.x);
-                acc[t][8 * v + 2] += gy * bf_lo(w.y);
-                acc[t][8 * v + 3] += gy * bf_hi(w.y);
-                acc[t][8 * v + 4] += gy * bf_lo(w.z);
-                acc[t][8 * v + 5] += gy * bf_hi(w.z);
-                acc[t][8 * v + 6] += gy * bf_lo(w.w);
-                acc[t][8 * v + 7] += gy * bf_hi(w.w);
+                    for (int co = 0; co < CO; ++co) out[((size_t)tap * CO + co) * CI + ci] = __uint_as_float(r[co]);
+                }
             }
         }
     }
-    // partial layout per CTA: [27][CO][CI] then [CO] biases
-    float* out = partial + (size_t)blockIdx.x * (27 * CO * CI + CO);
-    if (co_ok) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int tap = g + 8 * t;
-            if (tap >= 27) continue;
-#pragma unroll
-            for (int c = 0; c < CI; ++c) out[((size_t)tap * CO + co) * CI + c] = acc[t][c];
-        }
-        if (g == 0) out[27 * CO * CI + co] = db;
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, Lay::TCOLS);
+    }
+}
+
+// Bias gradient db[co] = sum_p dY[p][co], one partial per CTA written beside
+// the weight partial ([27][CO][CI] then [CO]).
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) bias_grad(const __nv_bfloat16* __restrict__ dY, float* __restrict__ partial,
+                                                 long P) {
+    __shared__ float sh[256];
+    const int co = threadIdx.x % CO, grp = threadIdx.x / CO;
+    constexpr int NGRP = 256 / CO;
+    const long chunk = (P + gridDim.x - 1) / gridDim.x;
+    const long p0 = blockIdx.x * chunk, p1 = min(P, p0 + chunk);
+    const unsigned short* d = reinterpret_cast<const unsigned short*>(dY);
+    float a = 0.f;
+    for (long p = p0 + grp; p < p1; p += NGRP) a += __uint_as_float((uint32_t)__ldg(d + p * CO + co) << 16);
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    if (grp == 0) {
+        float s = 0.f;
+        for (int k = 0; k < NGRP; ++k) s += sh[k * CO + co];
+        partial[(size_t)blockIdx.x * (27 * CO * CI + CO) + 27 * CO * CI + co] = s;
     }
 }
 
@@ -375,6 +689,15 @@ struct lbm_cnn {
     double* u_d;
     double* lpart;               // loss partials
     double* lsum;
+    int* status;                 // device status word (bounded-wait timeouts)
+    int nsm = 0;                 // multiprocessors of the device
+    int wg_blocks = 0;           // CTAs of the weight-gradient kernels (one partial each)
+    cnn::TileGeom geom;          // 128-voxel tiles of the grid
+    CUtensorMap m_act[cnn::NL];  // act[l] with CH[l] channels
+    CUtensorMap m_dA[2];         // dA[k] with 32 channels
+    CUtensorMap m_dY4;           // dA[1] read as [P][16] (gradient of the output layer)
+    CUtensorMap m_wf[cnn::NL];   // forward weights [27][CO][CI]
+    CUtensorMap m_wb[cnn::NL];   // backward-data weights [27][CI][CO] (layers 1..3)
     std::string err;
 };
 
@@ -404,28 +727,126 @@ size_t layer_offset(int l) {
     return o;
 }
 
-template <int CI, int CO, int EPI>
-cudaError_t conv(lbm_cnn* c, const __nv_bfloat16* X, const __nv_bfloat16* W, const float* bias, void* Y,
-                 const __nv_bfloat16* gate) {
-    const size_t smem = (size_t)27 * CO * CI * 2;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(cnn::conv_mma<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against libcuda).
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Box of one 128-voxel tile: powers of two, x first.
+cnn::TileGeom make_geom(int nx, int ny, int nz) {
+    auto p2 = [](int v) {
+        int r = 1;
+        while (r < v && r < 128) r <<= 1;
+        return r;
+    };
+    cnn::TileGeom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.bx = p2(nx);
+    g.by = std::min(128 / g.bx, p2(ny));
+    g.bz = 128 / (g.bx * g.by);
+    g.ntx = (nx + g.bx - 1) / g.bx;
+    g.nty = (ny + g.by - 1) / g.by;
+    g.ntz = (nz + g.bz - 1) / g.bz;
+    g.ntiles = g.ntx * g.nty * g.ntz;
+    return g;
+}
+
+// Channel-last activation [nz][ny][nx][C] (BF16) as a 4D tensor map whose box
+// is one tile; 64-byte swizzle for 32 channels, 32-byte for 16.
+bool map_activation(CUtensorMap* m, const void* base, int C, const cnn::TileGeom& g) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)g.nx * C * 2, (cuuint64_t)g.nx * g.ny * C * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Packed weights [27][CO][CI] (BF16) as one 3D box holding all taps.
+bool map_weights(CUtensorMap* m, const void* base, int CI, int CO) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)CI, (cuuint64_t)CO, 27};
+    const cuuint64_t strides[2] = {(cuuint64_t)CI * 2, (cuuint64_t)CO * CI * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)CI, (cuuint32_t)CO, 27};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CI == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_maps(lbm_cnn* c) {
+    bool ok = true;
+    for (int l = 0; l < cnn::NL; ++l) {
+        ok = ok && map_activation(&c->m_act[l], c->act[l], cnn::CH[l], c->geom);
+        ok = ok && map_weights(&c->m_wf[l], c->wf[l], cnn::CH[l], cnn::CH[l + 1]);
+        if (l > 0) ok = ok && map_weights(&c->m_wb[l], c->wb[l], cnn::CH[l + 1], cnn::CH[l]);
     }
-    const long blocks = (c->s.P + 255) / 256;
-    cnn::conv_mma<CI, CO, EPI><<<(unsigned)blocks, 128, smem, c->stream>>>(X, W, bias, Y, gate, c->s);
+    ok = ok && map_activation(&c->m_dA[0], c->dA[0], 32, c->geom);
+    ok = ok && map_activation(&c->m_dA[1], c->dA[1], 32, c->geom);
+    ok = ok && map_activation(&c->m_dY4, c->dA[1], 16, c->geom);
+    return ok;
+}
+
+template <int CI, int CO, int EPI>
+cudaError_t conv(lbm_cnn* c, const CUtensorMap& mapX, const CUtensorMap& mapW, const float* bias, void* Y,
+                 const __nv_bfloat16* gate) {
+    const int smem = cnn::ConvLayout<CI, CO, cnn::CONV_STAGES>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(cnn::conv_tc<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::min(c->geom.ntiles, 2 * c->nsm);
+    cnn::conv_tc<CI, CO, EPI><<<blocks, 192, smem, c->stream>>>(mapX, mapW, bias, Y, gate, c->geom, c->status);
     return cudaGetLastError();
 }
 
 template <int CI, int CO>
-cudaError_t wgrad(lbm_cnn* c, const __nv_bfloat16* X, const __nv_bfloat16* dY, float* gpad) {
-    cnn::conv_wgrad<CI, CO><<<cnn::WG_BLOCKS, 256, 0, c->stream>>>(X, dY, c->partial, c->s);
+cudaError_t wgrad(lbm_cnn* c, const CUtensorMap& mapX, const CUtensorMap& mapY, const __nv_bfloat16* dY,
+                  float* gpad) {
+    const int smem = cnn::WgLayout<CI, CO>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(cnn::wgrad_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cnn::wgrad_tc<CI, CO><<<c->wg_blocks, 192, smem, c->stream>>>(mapX, mapY, c->partial, c->geom, c->status);
+    cnn::bias_grad<CI, CO><<<c->wg_blocks, 256, 0, c->stream>>>(dY, c->partial, c->s.P);
     const int width = 27 * CO * CI + CO;
-    cnn::sum_partials<<<(width + 255) / 256, 256, 0, c->stream>>>(c->partial, cnn::WG_BLOCKS, width, gpad);
+    cnn::sum_partials<<<(width + 255) / 256, 256, 0, c->stream>>>(c->partial, c->wg_blocks, width, gpad);
     return cudaGetLastError();
+}
+
+// Device status word -> lbm_status (after a stream synchronisation).
+lbm_status check_status(lbm_cnn* c, const char* where) {
+    int st = 0;
+    if (cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string(where) + ": status read failed";
+        return LBM_ERR_CUDA;
+    }
+    if (st != 0) {
+        c->err = std::string(where) + ": a tensor-core pipeline wait ran out of time";
+        return (lbm_status)st;
+    }
+    return LBM_OK;
 }
 
 cudaError_t pack_all(lbm_cnn* c) {
@@ -440,23 +861,23 @@ cudaError_t pack_all(lbm_cnn* c) {
 }
 
 cudaError_t forward(lbm_cnn* c) {
-    cudaError_t e = conv<16, 32, 0>(c, c->act[0], c->wf[0], c->bias[0], c->act[1], nullptr);
-    if (e == cudaSuccess) e = conv<32, 32, 0>(c, c->act[1], c->wf[1], c->bias[1], c->act[2], nullptr);
-    if (e == cudaSuccess) e = conv<32, 32, 0>(c, c->act[2], c->wf[2], c->bias[2], c->act[3], nullptr);
-    if (e == cudaSuccess) e = conv<32, 16, 1>(c, c->act[3], c->wf[3], c->bias[3], c->out, nullptr);
+    cudaError_t e = conv<16, 32, 0>(c, c->m_act[0], c->m_wf[0], c->bias[0], c->act[1], nullptr);
+    if (e == cudaSuccess) e = conv<32, 32, 0>(c, c->m_act[1], c->m_wf[1], c->bias[1], c->act[2], nullptr);
+    if (e == cudaSuccess) e = conv<32, 32, 0>(c, c->m_act[2], c->m_wf[2], c->bias[2], c->act[3], nullptr);
+    if (e == cudaSuccess) e = conv<32, 16, 1>(c, c->m_act[3], c->m_wf[3], c->bias[3], c->out, nullptr);
     return e;
 }
 
 // Backward from dY4 (held in dA[1] reinterpreted as [P][16]); fills c->grad.
 cudaError_t backward(lbm_cnn* c, const __nv_bfloat16* dY4) {
-    cudaError_t e = wgrad<32, 16>(c, c->act[3], dY4, c->gpad[3]);
+    cudaError_t e = wgrad<32, 16>(c, c->m_act[3], c->m_dY4, dY4, c->gpad[3]);
     // dA3 = conv^T(dY4, W4) masked by act3 > 0
-    if (e == cudaSuccess) e = conv<16, 32, 2>(c, dY4, c->wb[3], nullptr, c->dA[0], c->act[3]);
-    if (e == cudaSuccess) e = wgrad<32, 32>(c, c->act[2], c->dA[0], c->gpad[2]);
-    if (e == cudaSuccess) e = conv<32, 32, 2>(c, c->dA[0], c->wb[2], nullptr, c->dA[1], c->act[2]);
-    if (e == cudaSuccess) e = wgrad<32, 32>(c, c->act[1], c->dA[1], c->gpad[1]);
-    if (e == cudaSuccess) e = conv<32, 32, 2>(c, c->dA[1], c->wb[1], nullptr, c->dA[0], c->act[1]);
-    if (e == cudaSuccess) e = wgrad<16, 32>(c, c->act[0], c->dA[0], c->gpad[0]);
+    if (e == cudaSuccess) e = conv<16, 32, 2>(c, c->m_dY4, c->m_wb[3], nullptr, c->dA[0], c->act[3]);
+    if (e == cudaSuccess) e = wgrad<32, 32>(c, c->m_act[2], c->m_dA[0], c->dA[0], c->gpad[2]);
+    if (e == cudaSuccess) e = conv<32, 32, 2>(c, c->m_dA[0], c->m_wb[2], nullptr, c->dA[1], c->act[2]);
+    if (e == cudaSuccess) e = wgrad<32, 32>(c, c->m_act[1], c->m_dA[1], c->dA[1], c->gpad[1]);
+    if (e == cudaSuccess) e = conv<32, 32, 2>(c, c->m_dA[1], c->m_wb[1], nullptr, c->dA[0], c->act[1]);
+    if (e == cudaSuccess) e = wgrad<16, 32>(c, c->m_act[0], c->m_dA[0], c->dA[0], c->gpad[0]);
     for (int l = 0; l < cnn::NL && e == cudaSuccess; ++l) {
         const int n = 27 * cnn::CH_REAL[l] * cnn::CH_REAL[l + 1];
         cnn::unpack_grad<<<(n + 255) / 256, 256, 0, c->stream>>>(c->gpad[l], c->grad + layer_offset(l),
@@ -516,6 +937,14 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
     c->s.nz = nz;
     c->s.P = (long)nx * ny * nz;
     c->stream = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LBM_ERR_CUDA;
+    }
+    c->wg_blocks = c->nsm;
+    c->geom = make_geom(nx, ny, nz);
     const size_t NP = lbm_cnn_param_count();
     const size_t Pn = (size_t)c->s.P;
     bool ok = true;
@@ -538,7 +967,7 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
         maxw = std::max(maxw, w + (size_t)cnn::CH[l + 1]);
         c->act[l] = (__nv_bfloat16*)A(Pn * cnn::CH[l] * 2);
     }
-    c->partial = (float*)A((size_t)cnn::WG_BLOCKS * maxw * 4);
+    c->partial = (float*)A((size_t)c->wg_blocks * maxw * 4);
     c->out = (float*)A(Pn * 16 * 4);
     c->dA[0] = (__nv_bfloat16*)A(Pn * 32 * 2);
     c->dA[1] = (__nv_bfloat16*)A(Pn * 32 * 2);
@@ -546,9 +975,14 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
     c->u_d = (double*)A(3 * Pn * 8);
     c->lpart = (double*)A(((Pn + 255) / 256) * 8);
     c->lsum = (double*)A(8);
+    c->status = (int*)A(256);
     if (!ok) {
         lbm_cnn_destroy(c);
         return LBM_ERR_OOM;
+    }
+    if (!make_maps(c)) {
+        lbm_cnn_destroy(c);
+        return LBM_ERR_CUDA;
     }
     cudaError_t e = cudaSuccess;
     if (init_weights) {
@@ -573,6 +1007,7 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
         e = cudaMemcpyAsync(c->master, w.data(), NP * 4, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 256, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_m, 0, NP * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v, 0, NP * 4, c->stream);
     for (int l = 0; l < cnn::NL && e == cudaSuccess; ++l)
@@ -591,8 +1026,8 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
 void lbm_cnn_destroy(lbm_cnn* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->master, c->grad,  c->adam_m, c->adam_v, c->partial, c->out, c->dA[0],
-                    c->dA[1],  c->rho_d, c->u_d,    c->lpart,  c->lsum};
+    void* ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->partial, c->out,   c->dA[0],
+                    c->dA[1],  c->rho_d, c->u_d,  c->lpart,  c->lsum,    c->status};
     for (void* p : ptrs) cnn_free(c, p);
     for (int l = 0; l < cnn::NL; ++l) {
         cnn_free(c, c->wf[l]);
@@ -653,7 +1088,7 @@ lbm_status lbm_cnn_forward(lbm_cnn* c, float* out, size_t count) {
         e = cudaMemcpy2DAsync(out, 4 * sizeof(float), c->out, 16 * sizeof(float), 4 * sizeof(float), (size_t)c->s.P,
                               cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? LBM_OK : cnn_cuda_fail(c, e, "lbm_cnn_forward");
+    return e == cudaSuccess ? check_status(c, "lbm_cnn_forward") : cnn_cuda_fail(c, e, "lbm_cnn_forward");
 }
 
 lbm_status lbm_cnn_gradient(lbm_cnn* c, const double* rho, const double* u, double* loss_out, float* grad_out,
@@ -671,6 +1106,8 @@ lbm_status lbm_cnn_gradient(lbm_cnn* c, const double* rho, const double* u, doub
         e = cudaMemcpyAsync(grad_out, c->grad, count * 4, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cnn_cuda_fail(c, e, "lbm_cnn_gradient");
+    const lbm_status st = check_status(c, "lbm_cnn_gradient");
+    if (st != LBM_OK) return st;
     if (loss_out) *loss_out = l / (4.0 * (double)c->s.P);
     return LBM_OK;
 }
@@ -701,6 +1138,8 @@ lbm_status lbm_cnn_warm_start(lbm_cnn* c, lbm_ctx* ctx, double reynolds) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cnn_cuda_fail(c, e, "lbm_cnn_warm_start");
+    st = check_status(c, "lbm_cnn_warm_start");
+    if (st != LBM_OK) return st;
     return lbm_init_fields(ctx, c->rho_d, c->u_d, nullptr, nullptr);
 }
 
