@@ -111,8 +111,8 @@ typedef struct {
 /* Body force F = (rho - rho_ref) g (Eq. eq:posColl0): a constant acceleration
  * for rho_ref = 0; the Rayleigh-Taylor test of Sec. III.H drives its two fluids
  * with rho_ref = (rho_h + rho_l)/2.  rho_ref != 0 is accepted by the two-phase
- * modules (LBM_PHYS_CGM, LBM_PHYS_SC); the other modules and the batch return
- * LBM_ERR_UNSUPPORTED for it. */
+ * modules (LBM_PHYS_CGM, LBM_PHYS_SC, and colour-gradient batches); the other
+ * modules return LBM_ERR_UNSUPPORTED for it. */
 typedef struct {
     double g[3];
     double rho_ref;
@@ -198,13 +198,18 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes);
 
 /* ---- Batched parameter sweeps ---------------------------------------------
- * Many independent domains (uneven sizes, per-domain omega, force, wall field)
- * advanced together: each lbm_batch_step runs ONE persistent cooperative
- * kernel that performs all n steps with a bounded-wait grid barrier between
- * steps, replayed from a CUDA graph captured on first use (per step count and
- * buffer parity).  Physics: LBM_PHYS_FLUID or LBM_PHYS_MHD; FP64 or FP32.
- * grids/relax/forcing/phys are arrays of ndomains entries (forcing may be NULL,
- * rho_ref must be 0; phys is required for MHD).  Domain d is initialised, read back, reduced and
+ * Many independent domains (uneven sizes, per-domain omega, force, wall field,
+ * density ratio, surface tension) advanced together: each lbm_batch_step runs
+ * ONE persistent cooperative kernel that performs all n steps with a
+ * bounded-wait grid barrier between steps, replayed from a CUDA graph captured
+ * on first use (per step count and buffer parity).  Physics: LBM_PHYS_FLUID,
+ * LBM_PHYS_MHD or LBM_PHYS_CGM (App. E colour gradient: its two passes per step,
+ * order parameter then collision, are separated by a second grid barrier; the
+ * batch holds the phi and rho_r planes of all domains); FP64 or FP32.
+ * grids/relax/forcing/phys are arrays of ndomains entries (forcing may be NULL;
+ * rho_ref must be 0 except for LBM_PHYS_CGM; phys is required for MHD and CGM,
+ * whose alpha_r, alpha_b, A, beta are taken per domain; the colour gradient has
+ * no moving lid).  Domain d is initialised, read back, reduced and
  * checkpointed through its view (lbm_batch_domain), which accepts
  * lbm_init_fields, lbm_fields, lbm_reduce and lbm_get/set_populations; the view
  * is owned by the batch (lbm_destroy on it does nothing, lbm_step on it is

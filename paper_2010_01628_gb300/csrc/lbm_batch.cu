@@ -7,8 +7,10 @@
 // nodes (x fastest); tiles of all domains form one global index space that the
 // resident CTAs walk with a grid stride.  A CTA finds its tile's domain by a
 // binary search over the per-domain first-tile table (uniform across the CTA).
-// Per-domain parameters (size, boundaries, omega, g, Hartmann field...) come
-// from a small device table.
+// Per-domain parameters (size, boundaries, omega, g, Hartmann field, colour
+// densities and surface tension...) come from a small device table.  The
+// colour-gradient step takes two passes (order parameter, then collision), so
+// its kernel runs a grid-wide barrier after each pass.
 //
 // The barrier waits are bounded: a CTA that waits longer than the timeout
 // records LBM_ERR_TIMEOUT and every CTA returns; the host reads the status at
@@ -22,6 +24,7 @@
 #include <new>
 #include <vector>
 
+#include "lbm_cgm.cuh"
 #include "lbm_fluid.cuh"
 #include "lbm_internal.h"
 #include "lbm_mhd.cuh"
@@ -31,7 +34,9 @@ namespace lbm {
 struct BatchDomain {
     FluidArgs fl;     // box, omega, g, lid
     MhdArgs mh;       // box, omega, tau_m, g, b_wall
+    CgmArgs cg;       // box, omega, alpha_r, alpha_b, A, beta, g, rho_ref g
     size_t off;       // element offset of the domain's plane 0 in a state copy
+    size_t soff;      // offset of the domain's node 0 in each scratch plane (colour gradient)
     uint32_t tile0;   // first global tile of the domain
     uint32_t ntiles;
 };
@@ -90,36 +95,73 @@ __device__ bool grid_barrier(BarrierState* bs, unsigned expected, unsigned long 
     return ok != 0;
 }
 
+// Domain of global tile t (binary search over the first-tile table; uniform
+// across the CTA) and the node's coordinates; false past the domain's end.
+__device__ __forceinline__ bool tile_node(const BatchDomain* __restrict__ doms, int nd, uint32_t t, int& d, int& x,
+                                          int& y, int& z) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (doms[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    d = lo;
+    const Box& b = doms[lo].fl.box;
+    const uint32_t cell = (t - doms[lo].tile0) * blockDim.x + threadIdx.x;
+    if (cell >= (uint32_t)b.n) return false;
+    const uint32_t plane = (uint32_t)b.nx * (uint32_t)b.ny;
+    const uint32_t zz = cell / plane;
+    const uint32_t r = cell - zz * plane;
+    const uint32_t yy = r / (uint32_t)b.nx;
+    x = (int)(r - yy * (uint32_t)b.nx);
+    y = (int)yy;
+    z = (int)zz;
+    return true;
+}
+
+// scratch (colour gradient only): phi of every domain's nodes, then rho_r,
+// each `scratch_n` values long; a domain's nodes start at its soff.
 template <int PHYS, typename S, typename C>
 __global__ void __launch_bounds__(256) batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
                                                     uint32_t ntiles, long nsteps, int parity0, int dry,
-                                                    BarrierState* bs, unsigned long long timeout_ns) {
+                                                    BarrierState* bs, unsigned long long timeout_ns, C* scratch,
+                                                    size_t scratch_n) {
     for (long s = 0; s < nsteps; ++s) {
         const int par = dry ? parity0 : (int)((parity0 + s) & 1);
         const S* src = par ? bufB : bufA;
         S* dst = par ? bufA : bufB;
-        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            int lo = 0, hi = nd - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (doms[mid].tile0 <= t)
-                    lo = mid;
-                else
-                    hi = mid - 1;
+        if (PHYS == LBM_PHYS_CGM) {
+            // pass 1: order parameter and red density of every node
+            for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int d, x, y, z;
+                if (tile_node(doms, nd, t, d, x, y, z)) {
+                    const BatchDomain& D = doms[d];
+                    cgm_phi_node<S, C, true, false>(src + D.off, scratch + D.soff, scratch + scratch_n + D.soff, D.cg,
+                                                    x, y, z);
+                }
             }
-            const BatchDomain& D = doms[lo];
-            const Box& b = D.fl.box;
-            const uint32_t cell = (t - D.tile0) * blockDim.x + threadIdx.x;
-            if (cell < (uint32_t)b.n) {
-                const uint32_t plane = (uint32_t)b.nx * (uint32_t)b.ny;
-                const uint32_t z = cell / plane;
-                const uint32_t r = cell - z * plane;
-                const uint32_t y = r / (uint32_t)b.nx;
-                const uint32_t x = r - y * (uint32_t)b.nx;
-                if (PHYS == LBM_PHYS_MHD)
-                    mhd_node<S, C, true, false>(src + D.off, dst + D.off, D.mh, (int)x, (int)y, (int)z);
-                else
-                    fluid_node<S, C, true, false>(src + D.off, dst + D.off, D.fl, (int)x, (int)y, (int)z);
+            if (!grid_barrier(bs, gridDim.x, timeout_ns)) return;
+            // pass 2: collision, perturbation, recolouring
+            for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int d, x, y, z;
+                if (tile_node(doms, nd, t, d, x, y, z)) {
+                    const BatchDomain& D = doms[d];
+                    cgm_collide_node<S, C, true, false>(src + D.off, dst + D.off, scratch + D.soff,
+                                                        scratch + scratch_n + D.soff, D.cg, x, y, z);
+                }
+            }
+        } else {
+            for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int d, x, y, z;
+                if (tile_node(doms, nd, t, d, x, y, z)) {
+                    const BatchDomain& D = doms[d];
+                    if (PHYS == LBM_PHYS_MHD)
+                        mhd_node<S, C, true, false>(src + D.off, dst + D.off, D.mh, x, y, z);
+                    else
+                        fluid_node<S, C, true, false>(src + D.off, dst + D.off, D.fl, x, y, z);
+                }
             }
         }
         if (s + 1 < nsteps && !grid_barrier(bs, gridDim.x, timeout_ns)) return;
@@ -155,6 +197,7 @@ struct BatchState {
     long graph_n[2] = {-1, -1};
     bool graph_ok = true;
     size_t state_elems = 0;
+    size_t scratch_n = 0;  // values per scratch plane (colour gradient: all domains' nodes)
     unsigned long long timeout_ns = lbm::BARRIER_TIMEOUT_NS;
 };
 
@@ -166,9 +209,15 @@ void* kernel_ptr() {
 }
 
 void* batch_kernel_for(const lbm_ctx* c) {
-    const bool mhd = c->physics == LBM_PHYS_MHD;
-    if (c->prec == LBM_FP64) return mhd ? kernel_ptr<LBM_PHYS_MHD, double, double>() : kernel_ptr<0, double, double>();
-    return mhd ? kernel_ptr<LBM_PHYS_MHD, float, float>() : kernel_ptr<0, float, float>();
+    const bool f64 = c->prec == LBM_FP64;
+    switch (c->physics) {
+        case LBM_PHYS_MHD:
+            return f64 ? kernel_ptr<LBM_PHYS_MHD, double, double>() : kernel_ptr<LBM_PHYS_MHD, float, float>();
+        case LBM_PHYS_CGM:
+            return f64 ? kernel_ptr<LBM_PHYS_CGM, double, double>() : kernel_ptr<LBM_PHYS_CGM, float, float>();
+        default:
+            return f64 ? kernel_ptr<0, double, double>() : kernel_ptr<0, float, float>();
+    }
 }
 
 void build_tiles(BatchState* B) {
@@ -214,7 +263,9 @@ cudaError_t launch_direct(lbm_ctx* c, cudaStream_t st, long n, int parity, int d
     uint32_t nt = B->ntiles;
     BarrierState* bar = B->d_bar;
     unsigned long long to = B->timeout_ns;
-    void* args[] = {&a, &b, &doms, &nd, &nt, &n, &parity, &dry, &bar, &to};
+    void* scratch = c->phi;  // colour gradient: phi and rho_r planes of all domains (else unused)
+    size_t scratch_n = B->scratch_n;
+    void* args[] = {&a, &b, &doms, &nd, &nt, &n, &parity, &dry, &bar, &to, &scratch, &scratch_n};
     return cudaLaunchCooperativeKernel(batch_kernel_for(c), dim3(B->grid), dim3(B->threads), args, 0, st);
 }
 
@@ -316,10 +367,10 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
                             lbm_precision precision, void* cuda_stream) {
     if (!out || ndomains < 1 || !grids || !relax) return LBM_ERR_ARG;
     *out = nullptr;
-    if (physics != LBM_PHYS_FLUID && physics != LBM_PHYS_MHD) return LBM_ERR_UNSUPPORTED;
+    if (physics != LBM_PHYS_FLUID && physics != LBM_PHYS_MHD && physics != LBM_PHYS_CGM) return LBM_ERR_UNSUPPORTED;
     if (precision != LBM_FP32 && precision != LBM_FP64) return LBM_ERR_UNSUPPORTED;
-    if (physics == LBM_PHYS_MHD && !phys) return LBM_ERR_ARG;
-    const int planes = physics == LBM_PHYS_MHD ? 40 : 19;
+    if ((physics == LBM_PHYS_MHD || physics == LBM_PHYS_CGM) && !phys) return LBM_ERR_ARG;
+    const int planes = physics == LBM_PHYS_MHD ? 40 : (physics == LBM_PHYS_CGM ? 24 : 19);
     const size_t elem = precision == LBM_FP64 ? 8 : 4;
     size_t total = 0, max_plane = 0, cells = 0;
     for (int d = 0; d < ndomains; ++d) {
@@ -331,10 +382,13 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
         if (relax[d].omega_bulk != 1.0 || relax[d].omega_3 != 1.0 || relax[d].omega_4 != 1.0)
             return LBM_ERR_UNSUPPORTED;
         if (physics == LBM_PHYS_MHD && !(phys[d].tau_m > 0.5)) return LBM_ERR_ARG;
-        if (forcing && forcing[d].rho_ref != 0.0) return LBM_ERR_UNSUPPORTED;
+        if (physics == LBM_PHYS_CGM &&
+            !(phys[d].alpha_r >= 0.0 && phys[d].alpha_r < 1.0 && phys[d].alpha_b >= 0.0 && phys[d].alpha_b < 1.0))
+            return LBM_ERR_ARG;
+        if (forcing && forcing[d].rho_ref != 0.0 && physics != LBM_PHYS_CGM) return LBM_ERR_UNSUPPORTED;
         if (g.wall_model != LBM_WALL_BOUNCE_BACK || relax[d].moment_space != LBM_MOMENTS_CENTRAL)
             return LBM_ERR_UNSUPPORTED;
-        if (physics == LBM_PHYS_MHD && (g.periodic_mask & 2u) == 0 &&
+        if ((physics == LBM_PHYS_MHD || physics == LBM_PHYS_CGM) && (g.periodic_mask & 2u) == 0 &&
             (g.lid_u[0] != 0.0 || g.lid_u[1] != 0.0 || g.lid_u[2] != 0.0))
             return LBM_ERR_UNSUPPORTED;
         const size_t nn = (size_t)g.nx * g.ny * g.nz;
@@ -372,11 +426,12 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
         return st;
     }
     B->state_elems = total;
+    B->scratch_n = cells;
     cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, c->device);
     cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
-    size_t off = 0, uoff = 0;
+    size_t off = 0, uoff = 0, soff = 0;
     for (int d = 0; d < ndomains && e == cudaSuccess; ++d) {
         const lbm_grid& g = grids[d];
         BatchDomain D;
@@ -402,7 +457,20 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
                 D.mh.bw[a] = phys[d].b_wall[a];
             }
         }
+        if (physics == LBM_PHYS_CGM) {
+            D.cg.box = D.fl.box;
+            D.cg.omega = relax[d].omega;
+            D.cg.alpha_r = phys[d].alpha_r;
+            D.cg.alpha_b = phys[d].alpha_b;
+            D.cg.A = phys[d].A;
+            D.cg.beta = phys[d].beta;
+            for (int a = 0; a < 3; ++a) {
+                D.cg.g[a] = D.fl.g[a];
+                D.cg.rg[a] = forcing ? forcing[d].rho_ref * forcing[d].g[a] : 0.0;
+            }
+        }
         D.off = off;
+        D.soff = soff;
         B->doms.push_back(D);
         // a view context per domain (init/fields/reduce/populations)
         lbm_ctx* v = new (std::nothrow) lbm_ctx();
@@ -423,10 +491,12 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
         v->buf[0] = (char*)c->buf[0] + off * elem;
         v->buf[1] = (char*)c->buf[1] + off * elem;
         v->uprev = (char*)c->uprev + uoff * (precision == LBM_FP64 ? 8 : 4);  // compute-type velocities
+        v->phi = c->phi ? (char*)c->phi + soff * (precision == LBM_FP64 ? 8 : 4) : nullptr;
         v->block_x = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32));
         B->views.push_back(v);
         off += ((size_t)planes * D.fl.box.n + 63) / 64 * 64;
         uoff += 3 * D.fl.box.n;
+        soff += D.fl.box.n;
     }
     if (e == cudaSuccess) e = configure(c);
     // rest state for every domain

@@ -177,8 +177,10 @@ __device__ __forceinline__ void gather19(const S* __restrict__ src, const Box& b
 }
 
 // Value of a node field v at x + c_I; a neighbour behind a wall contributes
-// the node's own value `own`.
-template <typename C, int I>
+// the node's own value `own`.  NC: read-only path (the field is not written
+// during the kernel); else an L2-coherent load (persistent kernels that
+// rewrite the field between grid-wide barriers).
+template <typename C, int I, bool NC = true>
 __device__ __forceinline__ C field_nbr(const C* __restrict__ v, const Box& b, const Nbr& q, int x, int y, int z,
                                        C own) {
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
@@ -188,7 +190,8 @@ __device__ __forceinline__ C field_nbr(const C* __restrict__ v, const Box& b, co
     const bool wall = (cx > 0 && q.wxp) || (cx < 0 && q.wxm) || (cy > 0 && q.wyp) || (cy < 0 && q.wym) ||
                       (cz > 0 && q.wzp) || (cz < 0 && q.wzm);
     if (wall) return own;
-    return __ldg(v + ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx);
+    const C* a = v + ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx;
+    return NC ? __ldg(a) : __ldcg(a);
 }
 
 // s = sum_i w_i c_i v(x + c_i) over the 18 moving directions: the lattice
@@ -373,10 +376,14 @@ __device__ __forceinline__ void raw_to_populations_q(const C (&r)[Q], C (&q)[Q])
 // storage loses no digits to the O(1) rest state.  The c_s^2 factors on the
 // k5/k6 terms of r16..18 follow from the expansion c = cbar + u.
 // QOUT: the result in the 16-bit units q = (f* - w)/w (raw_to_populations_q).
+// px, py, pz: the post-collision momentum r1..3* = rho u + h, passed in by the
+// caller as sum f c + F (the same value, without the division by rho and the
+// product with it: in FP32 that round trip biased the momentum of a uniformly
+// accelerated flow by 1e-5 of itself over 1000 steps).
 template <typename C, bool QOUT = false>
-__device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C hy, C hz, C k4, C r0c, C k4c,
-                                               const C (&kd)[5], const C (&t)[6], C k16c, C k17c, C k18c,
-                                               C (&f)[Q]) {
+__device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C hy, C hz, C px, C py, C pz, C k4,
+                                               C r0c, C k4c, const C (&kd)[5], const C (&t)[6], C k16c, C k17c,
+                                               C k18c, C (&f)[Q]) {
     const C third = (C)(1.0 / 3.0);
     const C x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
     const C k5 = kd[0], k6 = kd[1], k7 = kd[2], k8 = kd[3], k9 = kd[4];
@@ -387,9 +394,9 @@ __device__ __forceinline__ void back_transform(C rho, C ux, C uy, C uz, C hx, C 
 
     C r[Q];
     r[0] = r0c;
-    r[1] = rho * ux + hx;
-    r[2] = rho * uy + hy;
-    r[3] = rho * uz + hz;
+    r[1] = px;
+    r[2] = py;
+    r[3] = pz;
     r[4] = rho * (x2 + y2 + z2) + (C)2 * (ux * hx + uy * hy + uz * hz) + k4c;
     r[5] = rho * (x2 - y2) + (C)2 * (ux * hx - uy * hy) + k5;
     r[6] = rho * (y2 - z2) + (C)2 * (uy * hy - uz * hz) + k6;
@@ -450,7 +457,8 @@ __device__ __forceinline__ void collide_fluid(C (&f)[Q], const Moments<C>& m, co
     const C t[6] = {hy * third, hx * third, hz * third, hx * third, hz * third, hy * third};
     const C drho = m.drho;
     const C k16c = drho * (C)(1.0 / 9.0);
-    back_transform<C, QOUT>(rho, ux, uy, uz, hx, hy, hz, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+    back_transform<C, QOUT>(rho, ux, uy, uz, hx, hy, hz, m.jx + a.Fx, m.jy + a.Fy, m.jz + a.Fz, rho, drho, drho, kd,
+                            t, k16c, k16c, k16c, f);
 }
 
 // Raw-moment variant (App. C, N = I, T = M): r* = k* from the printed list, in
@@ -498,7 +506,8 @@ __device__ __forceinline__ void equilibrium_shifted(C rho, C drho, C ux, C uy, C
     const C kd[5] = {z, z, z, z, z};
     const C t[6] = {z, z, z, z, z, z};
     const C k16c = drho * (C)(1.0 / 9.0);
-    back_transform<C>(rho, ux, uy, uz, z, z, z, rho, drho, drho, kd, t, k16c, k16c, k16c, f);
+    back_transform<C>(rho, ux, uy, uz, z, z, z, rho * ux, rho * uy, rho * uz, rho, drho, drho, kd, t, k16c, k16c,
+                      k16c, f);
 }
 
 // ---------------------------------------------------------------------------

@@ -208,6 +208,24 @@ def hartmann_batch(ndomains=64, seed=2, sizes=(32, 48, 64, 96), ha_range=(1.0, 2
     return [(int(a), float(b)) for a, b in zip(n, ha)]
 
 
+def droplet_sweep(ndomains=64, seed=5, sizes=(32, 48, 64, 96), ratio_range=(2.0, 10.0)):
+    """Parameter sweep of cubic droplet boxes: (n_d, density ratio_d) pairs.
+    Each box is filled by droplets(n_d, seed + d, r_min = max(4, n_d/16),
+    r_max = max(6, n_d/8), rho_r0 = ratio_d, rho_b0 = 1) (the 256^3 recipe's
+    radii 8-24 scaled to the box)."""
+    rng = np.random.default_rng(seed)
+    n = rng.choice(np.array(sizes), size=ndomains)
+    ratio = rng.uniform(ratio_range[0], ratio_range[1], size=ndomains)
+    return [(int(a), float(b)) for a, b in zip(n, ratio)]
+
+
+def sweep_droplets(n, ratio, index, seed=5):
+    """Fields (rho, u, phase) of domain `index` of droplet_sweep."""
+    rho, u, phase, _, _ = droplets(n, seed=seed + index, r_min=max(4.0, n / 16.0), r_max=max(6.0, n / 8.0),
+                                   rho_r0=ratio, rho_b0=1.0)
+    return rho, u, phase
+
+
 def cavity_reynolds(count, seed=4, lo=100.0, hi=1000.0):
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=count)

@@ -49,3 +49,38 @@ def gpu_run(shape, omega, steps, rho, u, phase=None, B=None, precision="fp64", p
         if ctx:
             L.lbm_destroy(ctx)
 
+
+
+def round_bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def round_fp16(x):
+    """Round to the nearest FP16 value, returned as float64."""
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
+def oracle_run_stored(shape, omega, steps, rho, u, storage, **kw):
+    """The FP64 oracle with its populations rounded after initialisation and
+    after every step as the 16-bit storage formats hold them, q = (f - w)/w
+    rounded to BF16 or FP16 (through FP32): the error floor of the storage
+    format itself, with exact arithmetic in between."""
+    rnd = {"bf16": round_bf16, "fp16": round_fp16}[storage]
+    _, w = O.lattice()
+    d = O.Domain(shape, omega, **kw)
+    d.init(rho, u)
+
+    def store():
+        f = d.populations()
+        q = ((f - w) / w).astype(np.float32)
+        d.set_populations(w * (1.0 + rnd(q)))
+
+    store()
+    for _ in range(steps):
+        d.step(1)
+        store()
+    r, uu, _, _ = d.fields()
+    return {"rho": r, "u": uu}
