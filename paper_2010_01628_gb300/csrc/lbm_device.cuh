@@ -335,34 +335,57 @@ __device__ __forceinline__ void raw_to_populations(const C (&r)[Q], C (&f)[Q]) {
 // raw_to_populations with the result in the 16-bit formats' units,
 // q_i = (f_i - w_i)/w_i = 3 f_0, 18 f_i (axes), 36 f_i (diagonals): the 1/w_i
 // scaling rides on the constants of M^-1 instead of costing a multiply per
-// population.
+// population.  Each group of four diagonal directions shares its sums and
+// differences (e.g. q4, q5, q13, q14 = 9 (P +- D), 9 (P' +- S) with
+// P = r16 - r11, P' = r16 + r11, D = r7 - r10, S = r7 + r10), and each axis
+// pair its common part, which the packed two-node collision of the 16-bit
+// kernels, bound by FP32-pipe operations, needs.
 template <typename C>
 __device__ __forceinline__ void raw_to_populations_q(const C (&r)[Q], C (&q)[Q]) {
-    const C nine = (C)9, three = (C)3;
+    const C nine = (C)9, mnine = (C)-9, three = (C)3;
     const C ax = (r[4] + (C)2 * r[5] + r[6]) * three;
     const C ay = (r[4] - r[5] + r[6]) * three;
     const C az = (r[4] - r[5] - (C)2 * r[6]) * three;
     const C s1617 = r[16] + r[17], s1618 = r[16] + r[18], s1718 = r[17] + r[18];
     q[0] = (r[0] - r[4] + r[16] + s1718) * three;
-    const C bx = (r[11] + r[13]) * nine, by = (r[10] + r[15]) * nine, bz = (r[12] + r[14]) * nine;
-    q[1] = bx - (r[1] + s1617) * nine + ax;
-    q[10] = (r[1] - s1617) * nine - bx + ax;
-    q[2] = by - (r[2] + s1618) * nine + ay;
-    q[11] = (r[2] - s1618) * nine - by + ay;
-    q[3] = bz - (r[3] + s1718) * nine + az;
-    q[12] = (r[3] - s1718) * nine - bz + az;
-    q[4] = (r[7] + r[16] - r[10] - r[11]) * nine;
-    q[5] = (r[10] + r[16] - r[7] - r[11]) * nine;
-    q[13] = (r[7] + r[10] + r[11] + r[16]) * nine;
-    q[14] = (r[11] + r[16] - r[7] - r[10]) * nine;
-    q[6] = (r[8] + r[17] - r[12] - r[13]) * nine;
-    q[7] = (r[12] + r[17] - r[8] - r[13]) * nine;
-    q[15] = (r[8] + r[12] + r[13] + r[17]) * nine;
-    q[16] = (r[13] + r[17] - r[8] - r[12]) * nine;
-    q[8] = (r[9] + r[18] - r[14] - r[15]) * nine;
-    q[9] = (r[14] + r[18] - r[9] - r[15]) * nine;
-    q[17] = (r[9] + r[14] + r[15] + r[18]) * nine;
-    q[18] = (r[15] + r[18] - r[9] - r[14]) * nine;
+    // axes: q_+ = E - D, q_- = E + D with E = a - 9 s, D = 9 (r_b - r_1)
+    {
+        const C e = s1617 * mnine + ax, d = (r[11] + r[13] - r[1]) * nine;
+        q[1] = e + d;
+        q[10] = e - d;
+    }
+    {
+        const C e = s1618 * mnine + ay, d = (r[10] + r[15] - r[2]) * nine;
+        q[2] = e + d;
+        q[11] = e - d;
+    }
+    {
+        const C e = s1718 * mnine + az, d = (r[12] + r[14] - r[3]) * nine;
+        q[3] = e + d;
+        q[12] = e - d;
+    }
+    // face diagonals, four per plane
+    {
+        const C pm = (r[16] - r[11]) * nine, pp = (r[16] + r[11]) * nine, dm = r[7] - r[10], dp = r[7] + r[10];
+        q[4] = dm * nine + pm;
+        q[5] = dm * mnine + pm;
+        q[13] = dp * nine + pp;
+        q[14] = dp * mnine + pp;
+    }
+    {
+        const C pm = (r[17] - r[13]) * nine, pp = (r[17] + r[13]) * nine, dm = r[8] - r[12], dp = r[8] + r[12];
+        q[6] = dm * nine + pm;
+        q[7] = dm * mnine + pm;
+        q[15] = dp * nine + pp;
+        q[16] = dp * mnine + pp;
+    }
+    {
+        const C pm = (r[18] - r[15]) * nine, pp = (r[18] + r[15]) * nine, dm = r[9] - r[14], dp = r[9] + r[14];
+        q[8] = dm * nine + pm;
+        q[9] = dm * mnine + pm;
+        q[17] = dp * nine + pp;
+        q[18] = dp * mnine + pp;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -252,9 +252,12 @@ __device__ __forceinline__ float pull_q(const S* __restrict__ src, const Box& b,
     return v;
 }
 
+// At most 128 threads and 72 registers (7 CTAs, 28 warps per SM; 78 registers
+// left 6): the kernel waits on its 38 pulls, and the extra warps hide more of
+// that latency.
 template <typename S, bool WALLS>
-__global__ void __launch_bounds__(256) fluid_step_zpair_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                                                               FluidArgs p) {
+__global__ void __launch_bounds__(ZPAIR_MAX_THREADS, 7) fluid_step_zpair_kernel(const S* __restrict__ src,
+                                                                              S* __restrict__ dst, FluidArgs p) {
     const Box& b = p.box;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= b.nx) return;

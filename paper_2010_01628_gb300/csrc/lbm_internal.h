@@ -80,6 +80,8 @@ cudaError_t fluid_step(lbm_ctx* c, long n, bool dry = false);
 int fluid_tma_max_stages(const lbm_ctx* c, int ctas);
 // The 16-bit single-phase step with two nodes per thread and packed FP32x2
 // arithmetic (launch variants 2 and 4): D3Q19 central moments, bounce-back walls.
+// Threads per CTA of the z-pair kernel (launch variant 4), fixed by its launch bounds.
+constexpr int ZPAIR_MAX_THREADS = 128;
 inline bool packed16_ok(const lbm_ctx* c) {
     return c->physics == LBM_PHYS_FLUID && (c->prec == LBM_FP16_SHIFTED || c->prec == LBM_BF16_SHIFTED) &&
            c->grid.wall_model == LBM_WALL_BOUNCE_BACK && c->relax.moment_space == LBM_MOMENTS_CENTRAL && c->q == 19;

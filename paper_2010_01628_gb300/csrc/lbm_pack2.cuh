@@ -24,7 +24,12 @@ __device__ __forceinline__ float2 p2_sub(float2 a, float2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(p2_bits(a)), "l"(p2_bits(b)));
     return p2_from_bits(d);
 }
-__device__ __forceinline__ float2 p2_neg(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+// Sign flip of both lanes by an integer XOR: the ALU pipe does it, leaving the
+// FP32 pipe (which the packed collision keeps busy) to the arithmetic.
+__device__ __forceinline__ float2 p2_neg(float2 a) {
+    return make_float2(__uint_as_float(__float_as_uint(a.x) ^ 0x80000000u),
+                       __uint_as_float(__float_as_uint(a.y) ^ 0x80000000u));
+}
 
 struct P2 {
     float2 v;
@@ -68,7 +73,15 @@ __device__ __forceinline__ P2& P2::operator+=(P2 b) { return *this = *this + b; 
 __device__ __forceinline__ P2& P2::operator-=(P2 b) { return *this = *this - b; }
 __device__ __forceinline__ P2& P2::operator*=(P2 b) { return *this = P2(__fmul2_rn(v, b.v)); }
 
-// Correctly rounded reciprocal per lane (as the scalar FP32 path).
-__device__ __forceinline__ P2 recip(P2 x) { return P2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+// Reciprocal per lane by the hardware approximation (within about 1 ulp; the
+// argument is a density near 1): the correctly rounded form costs a refinement
+// and a special-case path on the FP32 pipe, which the 16-bit kernels are short
+// of, for a difference far below their storage rounding.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ P2 recip(P2 x) { return P2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
 
 }  // namespace lbm

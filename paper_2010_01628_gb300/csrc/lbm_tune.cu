@@ -170,6 +170,7 @@ extern "C" lbm_status lbm_set_launch_shape(lbm_ctx* c, int variant, int threads,
     if (variant == 0 || variant == 2 || variant == 4) {
         if (variant == 2 && !(lbm::packed16_ok(c) && c->box.nx % 2 == 0)) return LBM_ERR_UNSUPPORTED;
         if (variant == 4 && !lbm::packed16_ok(c)) return LBM_ERR_UNSUPPORTED;
+        if (variant == 4 && threads > lbm::ZPAIR_MAX_THREADS) return LBM_ERR_UNSUPPORTED;
         c->variant = variant;
         c->block_x = threads;
         return LBM_OK;
@@ -275,7 +276,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
         if (lbm::packed16_ok(c)) {
             if (c->box.nx % 2 == 0)
                 for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
-            for (int bx : {64, 128, 256}) cands.push_back({4, bx, 0, 1});
+            for (int bx : {64, 128}) cands.push_back({4, bx, 0, 1});  // z-pairs: at most 128 threads
         }
         for (int ctas : {1, 2, 3, 4}) {
             const int smax = lbm::fluid_tma_max_stages(c, ctas);

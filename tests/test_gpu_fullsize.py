@@ -1,6 +1,7 @@
 """Parity at the full workload sizes, in the launch configurations the
-benchmark times: the 64-domain Hartmann batch (one persistent graph-captured
-launch per call, autotuned shape) and the 256^3 colour-gradient droplets.
+benchmark times: the 64-domain Hartmann batch and the 64-domain droplet
+(density-ratio) batch (one persistent graph-captured launch per call,
+autotuned shape) and the 256^3 colour-gradient droplets.
 Outputs are checked on sampled domains or nodes the oracle can compute alone.
 """
 import numpy as np
@@ -48,6 +49,45 @@ def test_mhd_batch_64_domains_sampled():
         o = oracle_run(shapes[k], omega, steps, rho, u, B=B, physics="mhd", periodic=(True, False, True), g=gs[k],
                        b_wall=(0.0, b0s[k], 0.0), tau_m=tau_m, threads=None)
         for f in ("rho", "u", "B"):
+            assert rel_l2(outs[k][f], o[f]) <= 1e-5, (shapes[k], f)
+
+
+def test_cgm_batch_64_domains_sampled():
+    """The density-ratio sweep of the benchmark (64 droplet boxes, sizes
+    {32,48,64,96}^3, ratio U[2, 10]), FP32, autotuned, 5 steps; the first
+    domain of each size compared in full with the oracle.  Velocity noise of
+    1e-2 is added so that u is not the (tiny) spurious current alone."""
+    from paper_2010_01628_gb300 import binding as L
+    sweep = inputs.droplet_sweep(64, seed=5)
+    tau, sigma, alpha_b = 0.8, 1e-4, 1.0 / 3.0
+    om = 1.0 / tau
+    alpha_r = [1.0 - (1.0 - alpha_b) / r for _, r in sweep]
+    A = 9.0 * sigma * om / 4.0
+    shapes = [(n, n, n) for n, _ in sweep]
+    batch = L.lbm_batch_create(shapes, om, physics="cgm", precision="fp32", alpha_b=alpha_b, alpha_r=alpha_r, A=A,
+                               beta=0.7)
+    pick = {}
+    for k, (n, _) in enumerate(sweep):
+        pick.setdefault(n, k)
+    init = {}
+    try:
+        for k, (n, ratio) in enumerate(sweep):
+            rho, u, ph = inputs.sweep_droplets(n, ratio, k)
+            u = u + inputs.noise_box((n, n, n), amp=1e-2, seed=200 + k)[1]
+            if k in pick.values():
+                init[k] = (rho, u, ph)
+            L.lbm_init_fields(L.lbm_batch_domain(batch, k), rho, u, phase=ph)
+        L.lbm_autotune(batch, None)
+        L.lbm_batch_step(batch, 2)
+        L.lbm_batch_step(batch, 3)
+        L.lbm_sync(batch)
+        outs = {k: L.lbm_fields(L.lbm_batch_domain(batch, k), shapes[k], want=("rho", "u", "phase")) for k in init}
+    finally:
+        L.lbm_destroy(batch)
+    for k, (rho, u, ph) in init.items():
+        o = oracle_run(shapes[k], om, 5, rho, u, phase=ph, physics="cgm", alpha_r=alpha_r[k], alpha_b=alpha_b, A=A,
+                       beta=0.7)
+        for f in ("rho", "u", "phase"):
             assert rel_l2(outs[k][f], o[f]) <= 1e-5, (shapes[k], f)
 
 
