@@ -14,9 +14,9 @@
 //
 // The barrier waits are bounded: a CTA that waits longer than the timeout
 // records LBM_ERR_TIMEOUT and every CTA returns; the host reads the status at
-// the next lbm_sync.  The kernel reads its sources through L2 (ld.global.cg):
-// the buffers are rewritten between barriers, so the read-only L1 path is not
-// valid here.
+// the next lbm_sync.  The buffers are rewritten between barriers, so the
+// read-only (.nc) path is not valid here: the kernel uses plain cached loads,
+// which the barrier's GPU-scope fences order after the other CTAs' stores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -122,9 +122,13 @@ __device__ __forceinline__ bool tile_node(const BatchDomain* __restrict__ doms, 
 }
 
 // scratch (colour gradient only): phi of every domain's nodes, then rho_r,
-// each `scratch_n` values long; a domain's nodes start at its soff.
-template <int PHYS, typename S, typename C>
-__global__ void __launch_bounds__(256) batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
+// each `scratch_n` values long; a domain's nodes start at its soff.  WALLS:
+// false when every domain is periodic in all three directions (the node code
+// then carries no bounce-back).  The FP32 colour-gradient variant is held to
+// 64 registers (4 CTAs of 256 per SM; its order-parameter pass waits on 68
+// loads per node and needs the warps).
+template <int PHYS, typename S, typename C, bool WALLS>
+__global__ void __launch_bounds__(256, (PHYS == LBM_PHYS_CGM && sizeof(S) == 4) ? 4 : 1) batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
                                                     uint32_t ntiles, long nsteps, int parity0, int dry,
                                                     BarrierState* bs, unsigned long long timeout_ns, C* scratch,
                                                     size_t scratch_n) {
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(256) batch_kernel(S* bufA, S* bufB, const Batc
                 int d, x, y, z;
                 if (tile_node(doms, nd, t, d, x, y, z)) {
                     const BatchDomain& D = doms[d];
-                    cgm_phi_node<S, C, true, false>(src + D.off, scratch + D.soff, scratch + scratch_n + D.soff, D.cg,
+                    cgm_phi_node<S, C, WALLS, false>(src + D.off, scratch + D.soff, scratch + scratch_n + D.soff, D.cg,
                                                     x, y, z);
                 }
             }
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(256) batch_kernel(S* bufA, S* bufB, const Batc
                 int d, x, y, z;
                 if (tile_node(doms, nd, t, d, x, y, z)) {
                     const BatchDomain& D = doms[d];
-                    cgm_collide_node<S, C, true, false>(src + D.off, dst + D.off, scratch + D.soff,
+                    cgm_collide_node<S, C, WALLS, false>(src + D.off, dst + D.off, scratch + D.soff,
                                                         scratch + scratch_n + D.soff, D.cg, x, y, z);
                 }
             }
@@ -158,9 +162,9 @@ __global__ void __launch_bounds__(256) batch_kernel(S* bufA, S* bufB, const Batc
                 if (tile_node(doms, nd, t, d, x, y, z)) {
                     const BatchDomain& D = doms[d];
                     if (PHYS == LBM_PHYS_MHD)
-                        mhd_node<S, C, true, false>(src + D.off, dst + D.off, D.mh, x, y, z);
+                        mhd_node<S, C, WALLS, false>(src + D.off, dst + D.off, D.mh, x, y, z);
                     else
-                        fluid_node<S, C, true, false>(src + D.off, dst + D.off, D.fl, x, y, z);
+                        fluid_node<S, C, WALLS, false>(src + D.off, dst + D.off, D.fl, x, y, z);
                 }
             }
         }
@@ -198,25 +202,26 @@ struct BatchState {
     bool graph_ok = true;
     size_t state_elems = 0;
     size_t scratch_n = 0;  // values per scratch plane (colour gradient: all domains' nodes)
+    bool walls = true;     // false: every domain periodic in x, y and z
     unsigned long long timeout_ns = lbm::BARRIER_TIMEOUT_NS;
 };
 
 namespace {
 
 template <int PHYS, typename S, typename C>
-void* kernel_ptr() {
-    return (void*)lbm::batch_kernel<PHYS, S, C>;
+void* kernel_ptr(bool walls) {
+    return walls ? (void*)lbm::batch_kernel<PHYS, S, C, true> : (void*)lbm::batch_kernel<PHYS, S, C, false>;
 }
 
 void* batch_kernel_for(const lbm_ctx* c) {
-    const bool f64 = c->prec == LBM_FP64;
+    const bool f64 = c->prec == LBM_FP64, w = c->batch->walls;
     switch (c->physics) {
         case LBM_PHYS_MHD:
-            return f64 ? kernel_ptr<LBM_PHYS_MHD, double, double>() : kernel_ptr<LBM_PHYS_MHD, float, float>();
+            return f64 ? kernel_ptr<LBM_PHYS_MHD, double, double>(w) : kernel_ptr<LBM_PHYS_MHD, float, float>(w);
         case LBM_PHYS_CGM:
-            return f64 ? kernel_ptr<LBM_PHYS_CGM, double, double>() : kernel_ptr<LBM_PHYS_CGM, float, float>();
+            return f64 ? kernel_ptr<LBM_PHYS_CGM, double, double>(w) : kernel_ptr<LBM_PHYS_CGM, float, float>(w);
         default:
-            return f64 ? kernel_ptr<0, double, double>() : kernel_ptr<0, float, float>();
+            return f64 ? kernel_ptr<0, double, double>(w) : kernel_ptr<0, float, float>(w);
     }
 }
 
@@ -427,6 +432,8 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
     }
     B->state_elems = total;
     B->scratch_n = cells;
+    B->walls = false;
+    for (int d = 0; d < ndomains; ++d) B->walls = B->walls || (grids[d].periodic_mask & 7u) != 7u;
     cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, c->device);
     cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);

@@ -75,12 +75,12 @@ __device__ __forceinline__ C red_pop(C a, C vx, C vy, C vz, C f) {
     return fma_rn(a, f, (C)kappa * cv);
 }
 
-// NC: read-only path; else L2-coherent (persistent kernels whose sources are
-// rewritten between grid-wide barriers).
+// NC: read-only path; else a plain cached load (persistent kernels whose
+// sources are rewritten between grid-wide barriers).
 template <typename S, typename C, bool NC = true>
 __device__ __forceinline__ C cgm_ld(const S* __restrict__ src, size_t n, int plane, uint32_t cell) {
     const S* a = src + (size_t)plane * n + cell;
-    return (C)(NC ? Store<S>::load(a) : Store<S>::load_cg(a));
+    return (C)(NC ? Store<S>::load(a) : Store<S>::load_coherent(a));
 }
 
 // All 19 pulled populations of a node, f_I(x) = f*_I(x - c_I), and their red
@@ -204,7 +204,7 @@ __device__ __forceinline__ void cgm_phi_node(const S* __restrict__ src, C* __res
 template <typename C, bool NC = true>
 __device__ __forceinline__ void grad_phi(const C* __restrict__ phi, const Box& b, const Nbr& q, int x, int y, int z,
                                          uint32_t self, C (&gr)[3]) {
-    const C own = NC ? phi[self] : __ldcg(phi + self);
+    const C own = NC ? phi[self] : ld_coherent(phi + self);
     C ax = (C)0, ay = (C)0, az = (C)0, dx = (C)0, dy = (C)0, dz = (C)0;
 #define LBM_GP(I)                                                                           \
     {                                                                                       \
@@ -260,7 +260,7 @@ __device__ __forceinline__ void cgm_collide_node(const S* __restrict__ src, S* _
     C f[Q];
     gather19<S, C, WALLS, NC>(src, b, q, x, y, z, self, (C)0, (C)0, (C)0, f);
     const Moments<C> m = moments19(f);
-    const CgmNode<C> s = cgm_macro<C>(f, m, NC ? rho_red[self] : __ldcg(rho_red + self), p);
+    const CgmNode<C> s = cgm_macro<C>(f, m, NC ? rho_red[self] : ld_coherent(rho_red + self), p);
     cgm_collide<C>(f, m, s, (C)p.omega);
     C gr[3];
     grad_phi<C, NC>(phi, b, q, x, y, z, self, gr);

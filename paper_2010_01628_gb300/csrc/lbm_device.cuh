@@ -52,14 +52,34 @@ struct Box {
 // Storage formats.  FP64/FP32 hold f - w (shift by the rest state of rho0 = 1);
 // the 16-bit formats hold (f - w)/w so every direction uses the same range.
 template <typename S> struct Store;
+// Plain (weak, L1-cached) global loads in inline PTX, so that a const
+// __restrict__ source cannot be turned into a read-only (.nc) load.
+__device__ __forceinline__ double ld_coherent(const double* p) {
+    double v;
+    asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_coherent(const float* p) {
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned short ld_coherent(const unsigned short* p) {
+    unsigned short v;
+    asm volatile("ld.global.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
 // load(): read-only path (ld.global.nc), valid when the source buffer is not
-// written during the kernel.  load_cg(): L2-coherent load (ld.global.cg) for
-// kernels that rewrite their sources between grid-wide barriers.
+// written during the kernel.  load_coherent(): a plain cached load for
+// persistent kernels that rewrite their sources between grid-wide barriers:
+// the barrier's GPU-scope fences order it after the other CTAs' stores (the
+// read-only path has no such guarantee), and it still caches in L1, which the
+// neighbours' shared source values of the colour-gradient pull need.
 template <> struct Store<double> {
     static constexpr bool scaled = false;
     __device__ static __forceinline__ double to_float(double v) { return v; }
     __device__ static __forceinline__ double load(const double* p) { return __ldg(p); }
-    __device__ static __forceinline__ double load_cg(const double* p) { return __ldcg(p); }
+    __device__ static __forceinline__ double load_coherent(const double* p) { return ld_coherent(p); }
     __device__ static __forceinline__ void store(double* p, double v) { __stcs(p, v); }
 };
 template <> struct Store<float> {
@@ -72,10 +92,10 @@ template <> struct Store<float> {
         asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return v;
     }
-    // L2-coherent, with the same prefetch size (+1.2% on the batched persistent kernel)
-    __device__ static __forceinline__ float load_cg(const float* p) {
+    // cached, with the same prefetch size
+    __device__ static __forceinline__ float load_coherent(const float* p) {
         float v;
-        asm volatile("ld.global.cg.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        asm volatile("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return v;
     }
     __device__ static __forceinline__ void store(float* p, float v) { __stcs(p, v); }
@@ -84,21 +104,25 @@ template <> struct Store<__half> {
     static constexpr bool scaled = true;
     __device__ static __forceinline__ float to_float(__half v) { return __half2float(v); }
     __device__ static __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
-    __device__ static __forceinline__ float load_cg(const __half* p) { return __half2float(__ldcg(p)); }
+    __device__ static __forceinline__ float load_coherent(const __half* p) {
+        return __half2float(__ushort_as_half(ld_coherent(reinterpret_cast<const unsigned short*>(p))));
+    }
     __device__ static __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     static constexpr bool scaled = true;
     __device__ static __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
-    __device__ static __forceinline__ float load_cg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
+    __device__ static __forceinline__ float load_coherent(const __nv_bfloat16* p) {
+        return __uint_as_float((uint32_t)ld_coherent(reinterpret_cast<const unsigned short*>(p)) << 16);
+    }
     __device__ static __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // Read the shifted population f - w of direction I from storage.
 template <typename S, typename C, int I, bool NC = true>
 __device__ __forceinline__ C load_shifted(const S* p) {
-    C v = NC ? (C)Store<S>::load(p) : (C)Store<S>::load_cg(p);
+    C v = NC ? (C)Store<S>::load(p) : (C)Store<S>::load_coherent(p);
     if (Store<S>::scaled) v *= (C)w_of(I);
     return v;
 }
@@ -178,8 +202,8 @@ __device__ __forceinline__ void gather19(const S* __restrict__ src, const Box& b
 
 // Value of a node field v at x + c_I; a neighbour behind a wall contributes
 // the node's own value `own`.  NC: read-only path (the field is not written
-// during the kernel); else an L2-coherent load (persistent kernels that
-// rewrite the field between grid-wide barriers).
+// during the kernel); else a plain load (persistent kernels that rewrite the
+// field between grid-wide barriers; see Store::load_coherent).
 template <typename C, int I, bool NC = true>
 __device__ __forceinline__ C field_nbr(const C* __restrict__ v, const Box& b, const Nbr& q, int x, int y, int z,
                                        C own) {
@@ -191,7 +215,7 @@ __device__ __forceinline__ C field_nbr(const C* __restrict__ v, const Box& b, co
                       (cz > 0 && q.wzp) || (cz < 0 && q.wzm);
     if (wall) return own;
     const C* a = v + ((uint32_t)sz * (uint32_t)b.ny + (uint32_t)sy) * (uint32_t)b.nx + (uint32_t)sx;
-    return NC ? __ldg(a) : __ldcg(a);
+    return NC ? __ldg(a) : ld_coherent(a);
 }
 
 // s = sum_i w_i c_i v(x + c_i) over the 18 moving directions: the lattice

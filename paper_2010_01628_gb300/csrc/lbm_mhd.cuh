@@ -47,7 +47,7 @@ __device__ __forceinline__ void gather_mag_dir(const S* __restrict__ gsrc, const
     for (int a = 0; a < 3; ++a) {
         const S* p = (!WALLS || !wall) ? gsrc + (size_t)(3 * M + a) * b.n + cell
                                        : gsrc + (size_t)(3 * mopp(M) + a) * b.n + self;
-        const C v = NC ? (C)Store<S>::load(p) : (C)Store<S>::load_cg(p);
+        const C v = NC ? (C)Store<S>::load(p) : (C)Store<S>::load_coherent(p);
         g[M][a] = (!WALLS || !wall) ? v : -v + (C)(2.0 * mw(M)) * bw[a];
     }
 }
