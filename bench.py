@@ -230,6 +230,8 @@ def extra_workloads(L, torch, stream, steps, peak, only=None, domains=64, n_cgm=
         out.update(_cgm(L, timed, steps, peak, n_cgm, launch))
     if only in (None, "cgm_batch"):
         out.update(_cgm_batch(L, timed, steps, peak, domains, tune_cache))
+    if only in (None, "sc_batch"):
+        out.update(_sc_batch(L, timed, steps, peak, domains, tune_cache))
     if only in (None, "sc"):
         out.update(_sc(L, timed, steps, peak, (n_only,) if n_only else (100, 256), launch))
     if only in (None, "rt"):
@@ -412,6 +414,37 @@ def _cgm(L, timed, steps, peak, n, launch="auto"):
                                "launch": shape, "autotune_MLUPS": tuned, "achieved_GBps": ach,
                                "frac_of_hbm_peak": ach / peak, "note": CGM_NOTE}
     return out
+
+
+def _sc_batch(L, timed, steps, peak, domains=64, tune_cache="tmp"):
+    """Interaction-strength sweep: `domains` periodic static-bubble boxes, sizes {32,48,64,96}^3, G U[-5.5, -4.5]
+    (seed 6; the coexistence densities, hence the density ratio, follow G), radius n/4, nu = 0.0333, FP32, in one
+    persistent cooperative launch per call (pseudopotential pass, barrier, collision pass, barrier)."""
+    import tempfile
+    sweep = inputs.bubble_sweep(domains, seed=6)
+    shapes = [(n, n, n) for n, _ in sweep]
+    om = 1.0 / (3 * 0.0333 + 0.5)
+    batch = L.lbm_batch_create(shapes, om, physics="sc", precision="fp32", G=[g for _, g in sweep])
+    cells = sum(n ** 3 for n, _ in sweep)
+    for k, (n, _) in enumerate(sweep):
+        rho, u = inputs.static_bubble((n, n, n), n / 4.0)
+        L.lbm_init_fields(L.lbm_batch_domain(batch, k), rho, u)
+    cache = os.path.join(tempfile.gettempdir(), "lbm_tune_cache.json") if tune_cache == "tmp" else None
+    tuned = L.lbm_autotune(batch, cache)
+    L.lbm_batch_step(batch, 4)
+    n_b = max(20, steps)
+    t = timed(lambda n: L.lbm_batch_step(batch, n), n_b)
+    L.lbm_sync(batch)
+    info = L.lbm_batch_info(batch)
+    L.lbm_destroy(batch)
+    ach = 160 * cells * n_b / t / 1e9
+    return {f"sc_batch_{domains}": {
+        "MLUPS": cells * n_b / t / 1e6, "cells": cells, "steps": n_b, "bytes_per_lup": 160,
+        "moved_bytes_per_lup": 236, "achieved_GBps": ach, "frac_of_hbm_peak": ach / peak, "launch": info,
+        "autotune_MLUPS": tuned, "launches_per_call": 1,
+        "note": "Shan-Chen interaction-strength sweep in one persistent launch: two passes per step "
+                "(pseudopotential, then forced collision); 160 B/LUP algorithmic (populations read and written, psi "
+                "written and read once); the two passes move 236 B"}}
 
 
 def _sc(L, timed, steps, peak, sizes=(100, 256), launch="auto"):
@@ -738,8 +771,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--warm-cases", type=int, default=8,
                     help="held-out cavities timed warm vs cold (0: skip the measured warm-start arm)")
-    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "cgm_batch", "sc", "rt", "channel", "appd",
-                                       "fma-probe", "warmstart", "cnn"],
+    ap.add_argument("--only", choices=["tg32", "mhd_batch", "cgm", "cgm_batch", "sc", "sc_batch", "rt", "channel",
+                                       "appd", "fma-probe", "warmstart", "cnn"],
                     default=None,
                     help="run one secondary workload alone (profiling)")
     ap.add_argument("--domains", type=int, default=64, help="domains of the MHD batch workload")

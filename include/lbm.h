@@ -203,13 +203,15 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes);
  * ONE persistent cooperative kernel that performs all n steps with a
  * bounded-wait grid barrier between steps, replayed from a CUDA graph captured
  * on first use (per step count and buffer parity).  Physics: LBM_PHYS_FLUID,
- * LBM_PHYS_MHD or LBM_PHYS_CGM (App. E colour gradient: its two passes per step,
- * order parameter then collision, are separated by a second grid barrier; the
- * batch holds the phi and rho_r planes of all domains); FP64 or FP32.
- * grids/relax/forcing/phys are arrays of ndomains entries (forcing may be NULL;
- * rho_ref must be 0 except for LBM_PHYS_CGM; phys is required for MHD and CGM,
- * whose alpha_r, alpha_b, A, beta are taken per domain; the colour gradient has
- * no moving lid).  Domain d is initialised, read back, reduced and
+ * LBM_PHYS_MHD, LBM_PHYS_CGM (App. E colour gradient) or LBM_PHYS_SC (Sec.
+ * III.G Shan-Chen); the two-phase steps take two passes per step (order
+ * parameter or pseudopotential, then collision) separated by a second grid
+ * barrier, and the batch holds their phi and rho_r (psi) planes for all
+ * domains; FP64 or FP32.  grids/relax/forcing/phys are arrays of ndomains
+ * entries (forcing may be NULL; rho_ref must be 0 except for CGM and SC; phys
+ * is required for MHD, CGM and SC, whose tau_m and b_wall, alpha_r, alpha_b,
+ * A, beta, or G are taken per domain; the colour gradient and MHD have no
+ * moving lid).  Domain d is initialised, read back, reduced and
  * checkpointed through its view (lbm_batch_domain), which accepts
  * lbm_init_fields, lbm_fields, lbm_reduce and lbm_get/set_populations; the view
  * is owned by the batch (lbm_destroy on it does nothing, lbm_step on it is

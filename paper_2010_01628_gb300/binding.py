@@ -363,17 +363,18 @@ def _vectors(v, nd):
 
 def lbm_batch_create(shapes, omegas, *, periodic=(True, True, True), lid_u=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0),
                      physics="fluid", precision="fp32", tau_m=1.0, b_wall=(0.0, 0.0, 0.0), alpha_r=1.0 / 3.0,
-                     alpha_b=1.0 / 3.0, A=0.0, beta=0.7, rho_ref=0.0, stream=None):
+                     alpha_b=1.0 / 3.0, A=0.0, beta=0.7, G=0.0, rho_ref=0.0, stream=None):
     """Create a batch of len(shapes) domains; per-domain parameters may be
     given once (shared) or as lists of one entry per domain.  physics:
-    "fluid", "mhd" (tau_m, b_wall) or "cgm" (alpha_r, alpha_b, A, beta,
-    rho_ref: colour-gradient sweeps over density ratio and surface tension)."""
+    "fluid", "mhd" (tau_m, b_wall), "cgm" (alpha_r, alpha_b, A, beta,
+    rho_ref: colour-gradient sweeps over density ratio and surface tension)
+    or "sc" (G, rho_ref: Shan-Chen sweeps over the interaction strength)."""
     if _alloc_refs is None and _torch() is not None:
         lbm_set_allocator(True)
     nd = len(shapes)
     omegas = _scalars(omegas, nd)
     tau_m = _scalars(tau_m, nd)
-    alpha_r, alpha_b, A, beta, rho_ref = (_scalars(v, nd) for v in (alpha_r, alpha_b, A, beta, rho_ref))
+    alpha_r, alpha_b, A, beta, G, rho_ref = (_scalars(v, nd) for v in (alpha_r, alpha_b, A, beta, G, rho_ref))
     periodic = _vectors(periodic, nd)
     lid_u = _vectors(lid_u, nd)
     g = _vectors(g, nd)
@@ -388,7 +389,7 @@ def lbm_batch_create(shapes, omegas, *, periodic=(True, True, True), lid_u=(0.0,
         relax[d] = lbm_relax(float(omegas[d]), 1.0, 1.0, 1.0)
         phys[d].tau_m = float(tau_m[d])
         phys[d].alpha_r, phys[d].alpha_b = alpha_r[d], alpha_b[d]
-        phys[d].A, phys[d].beta = A[d], beta[d]
+        phys[d].A, phys[d].beta, phys[d].G = A[d], beta[d], G[d]
         forc[d].rho_ref = rho_ref[d]
         for a in range(3):
             grids[d].lid_u[a] = float(lid_u[d][a])

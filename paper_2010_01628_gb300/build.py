@@ -42,7 +42,7 @@ KERNEL_SOURCES = {
     "fluid": ["lbm_device.cuh", "lbm_fluid.cu"],
     "mhd": ["lbm_device.cuh", "lbm_mhd.cu"],
     "cgm": ["lbm_device.cuh", "lbm_cgm.cuh", "lbm_cgm.cu"],
-    "sc": ["lbm_device.cuh", "lbm_fluid.cuh", "lbm_sc.cu"],
+    "sc": ["lbm_device.cuh", "lbm_fluid.cuh", "lbm_sc.cuh", "lbm_sc.cu"],
     "q27": ["lbm_device.cuh", "lbm_q27.cu"],
 }
 

@@ -8,9 +8,10 @@
 // resident CTAs walk with a grid stride.  A CTA finds its tile's domain by a
 // binary search over the per-domain first-tile table (uniform across the CTA).
 // Per-domain parameters (size, boundaries, omega, g, Hartmann field, colour
-// densities and surface tension...) come from a small device table.  The
-// colour-gradient step takes two passes (order parameter, then collision), so
-// its kernel runs a grid-wide barrier after each pass.
+// densities and surface tension, Shan-Chen interaction strength...) come from
+// a small device table.  The colour-gradient and Shan-Chen steps take two
+// passes (order parameter or pseudopotential, then collision), so their
+// kernels run a grid-wide barrier after each pass.
 //
 // The barrier waits are bounded: a CTA that waits longer than the timeout
 // records LBM_ERR_TIMEOUT and every CTA returns; the host reads the status at
@@ -20,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -28,6 +30,7 @@
 #include "lbm_fluid.cuh"
 #include "lbm_internal.h"
 #include "lbm_mhd.cuh"
+#include "lbm_sc.cuh"
 
 namespace lbm {
 
@@ -35,6 +38,7 @@ struct BatchDomain {
     FluidArgs fl;     // box, omega, g, lid
     MhdArgs mh;       // box, omega, tau_m, g, b_wall
     CgmArgs cg;       // box, omega, alpha_r, alpha_b, A, beta, g, rho_ref g
+    ScArgs sc;        // box, omega, G, g, rho_ref g, lid
     size_t off;       // element offset of the domain's plane 0 in a state copy
     size_t soff;      // offset of the domain's node 0 in each scratch plane (colour gradient)
     uint32_t tile0;   // first global tile of the domain
@@ -136,7 +140,25 @@ __global__ void __launch_bounds__(256, (PHYS == LBM_PHYS_CGM && sizeof(S) == 4) 
         const int par = dry ? parity0 : (int)((parity0 + s) & 1);
         const S* src = par ? bufB : bufA;
         S* dst = par ? bufA : bufB;
-        if (PHYS == LBM_PHYS_CGM) {
+        if (PHYS == LBM_PHYS_SC) {
+            // pass 1: pseudopotential psi = 1 - exp(-rho) of every node
+            for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int d, x, y, z;
+                if (tile_node(doms, nd, t, d, x, y, z)) {
+                    const BatchDomain& D = doms[d];
+                    sc_psi_node<S, C, WALLS, false>(src + D.off, scratch + D.soff, D.sc, x, y, z);
+                }
+            }
+            if (!grid_barrier(bs, gridDim.x, timeout_ns)) return;
+            // pass 2: force, forced collision
+            for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                int d, x, y, z;
+                if (tile_node(doms, nd, t, d, x, y, z)) {
+                    const BatchDomain& D = doms[d];
+                    sc_collide_node<S, C, WALLS, false>(src + D.off, dst + D.off, scratch + D.soff, D.sc, x, y, z);
+                }
+            }
+        } else if (PHYS == LBM_PHYS_CGM) {
             // pass 1: order parameter and red density of every node
             for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 int d, x, y, z;
@@ -220,6 +242,8 @@ void* batch_kernel_for(const lbm_ctx* c) {
             return f64 ? kernel_ptr<LBM_PHYS_MHD, double, double>(w) : kernel_ptr<LBM_PHYS_MHD, float, float>(w);
         case LBM_PHYS_CGM:
             return f64 ? kernel_ptr<LBM_PHYS_CGM, double, double>(w) : kernel_ptr<LBM_PHYS_CGM, float, float>(w);
+        case LBM_PHYS_SC:
+            return f64 ? kernel_ptr<LBM_PHYS_SC, double, double>(w) : kernel_ptr<LBM_PHYS_SC, float, float>(w);
         default:
             return f64 ? kernel_ptr<0, double, double>(w) : kernel_ptr<0, float, float>(w);
     }
@@ -372,9 +396,10 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
                             lbm_precision precision, void* cuda_stream) {
     if (!out || ndomains < 1 || !grids || !relax) return LBM_ERR_ARG;
     *out = nullptr;
-    if (physics != LBM_PHYS_FLUID && physics != LBM_PHYS_MHD && physics != LBM_PHYS_CGM) return LBM_ERR_UNSUPPORTED;
+    if (physics != LBM_PHYS_FLUID && physics != LBM_PHYS_MHD && physics != LBM_PHYS_CGM && physics != LBM_PHYS_SC)
+        return LBM_ERR_UNSUPPORTED;
     if (precision != LBM_FP32 && precision != LBM_FP64) return LBM_ERR_UNSUPPORTED;
-    if ((physics == LBM_PHYS_MHD || physics == LBM_PHYS_CGM) && !phys) return LBM_ERR_ARG;
+    if ((physics == LBM_PHYS_MHD || physics == LBM_PHYS_CGM || physics == LBM_PHYS_SC) && !phys) return LBM_ERR_ARG;
     const int planes = physics == LBM_PHYS_MHD ? 40 : (physics == LBM_PHYS_CGM ? 24 : 19);
     const size_t elem = precision == LBM_FP64 ? 8 : 4;
     size_t total = 0, max_plane = 0, cells = 0;
@@ -390,7 +415,9 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
         if (physics == LBM_PHYS_CGM &&
             !(phys[d].alpha_r >= 0.0 && phys[d].alpha_r < 1.0 && phys[d].alpha_b >= 0.0 && phys[d].alpha_b < 1.0))
             return LBM_ERR_ARG;
-        if (forcing && forcing[d].rho_ref != 0.0 && physics != LBM_PHYS_CGM) return LBM_ERR_UNSUPPORTED;
+        if (physics == LBM_PHYS_SC && !std::isfinite(phys[d].G)) return LBM_ERR_ARG;
+        if (forcing && forcing[d].rho_ref != 0.0 && physics != LBM_PHYS_CGM && physics != LBM_PHYS_SC)
+            return LBM_ERR_UNSUPPORTED;
         if (g.wall_model != LBM_WALL_BOUNCE_BACK || relax[d].moment_space != LBM_MOMENTS_CENTRAL)
             return LBM_ERR_UNSUPPORTED;
         if ((physics == LBM_PHYS_MHD || physics == LBM_PHYS_CGM) && (g.periodic_mask & 2u) == 0 &&
@@ -474,6 +501,16 @@ lbm_status lbm_batch_create(lbm_ctx** out, int ndomains, const lbm_grid* grids, 
             for (int a = 0; a < 3; ++a) {
                 D.cg.g[a] = D.fl.g[a];
                 D.cg.rg[a] = forcing ? forcing[d].rho_ref * forcing[d].g[a] : 0.0;
+            }
+        }
+        if (physics == LBM_PHYS_SC) {
+            D.sc.box = D.fl.box;
+            D.sc.omega = relax[d].omega;
+            D.sc.G = phys[d].G;
+            for (int a = 0; a < 3; ++a) {
+                D.sc.g[a] = D.fl.g[a];
+                D.sc.rg[a] = forcing ? forcing[d].rho_ref * forcing[d].g[a] : 0.0;
+                D.sc.lid[a] = D.fl.lid[a];
             }
         }
         D.off = off;

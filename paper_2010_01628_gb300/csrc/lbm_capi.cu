@@ -168,9 +168,10 @@ lbm_status lbm_internal_alloc_batch(lbm_ctx* c, size_t state_elems, size_t cells
     c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
     c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
     if (!(c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging)) return LBM_ERR_OOM;
-    // colour gradient: phi and rho_r of every domain's nodes, rebuilt each step
-    if (c->physics == LBM_PHYS_CGM) {
-        c->phi = dev_alloc(c, 2 * cells * cb);
+    // colour gradient: phi and rho_r of every domain's nodes; Shan-Chen: psi;
+    // rebuilt each step
+    if (c->physics == LBM_PHYS_CGM || c->physics == LBM_PHYS_SC) {
+        c->phi = dev_alloc(c, (c->physics == LBM_PHYS_CGM ? 2 : 1) * cells * cb);
         if (!c->phi) return LBM_ERR_OOM;
     }
     if (cudaMallocHost((void**)&c->result_host, sizeof(double) * lbm::RED_WIDTH) != cudaSuccess) {

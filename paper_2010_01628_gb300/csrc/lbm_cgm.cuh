@@ -1,7 +1,8 @@
 // lbm_cgm.cuh -- device side of the colour-gradient two-phase step (App. E of
-// arXiv:2010.01628): node functions of its two passes, shared by the
-// single-domain kernels (lbm_cgm.cu) and the batched persistent kernel
-// (lbm_batch.cu).
+// arXiv:2010.01628): the pull, moments, collision, gradient, perturbation and
+// recolouring shared by the single-domain kernels (lbm_cgm.cu) and the
+// batched persistent kernel (lbm_batch.cu), and the node functions of the two
+// passes that the batch runs.
 //
 // Two passes per step.  Pass 1 pulls the populations of every node and writes
 // the order parameter phi = (rho_r - rho_b)/(rho_r + rho_b) (Eq. eq:order) and
@@ -79,8 +80,8 @@ __device__ __forceinline__ C red_pop(C a, C vx, C vy, C vz, C f) {
 // sources are rewritten between grid-wide barriers).
 template <typename S, typename C, bool NC = true>
 __device__ __forceinline__ C cgm_ld(const S* __restrict__ src, size_t n, int plane, uint32_t cell) {
-    const S* a = src + (size_t)plane * n + cell;
-    return (C)(NC ? Store<S>::load(a) : Store<S>::load_coherent(a));
+    if (NC) return (C)Store<S>::load(src + (size_t)plane * n + cell);
+    return (C)Store<S>::load_coherent(src + (size_t)plane * n + cell);
 }
 
 // All 19 pulled populations of a node, f_I(x) = f*_I(x - c_I), and their red

@@ -221,13 +221,13 @@ __device__ __forceinline__ C field_nbr(const C* __restrict__ v, const Box& b, co
 // s = sum_i w_i c_i v(x + c_i) over the 18 moving directions: the lattice
 // first moment of a node field (times 1/c_s^2 the isotropic gradient of the
 // colour-gradient model; times -G psi(x) the Shan-Chen force).
-template <typename C>
+template <typename C, bool NC = true>
 __device__ __forceinline__ void lattice_first_moment(const C* __restrict__ v, const Box& b, const Nbr& q, int x,
                                                      int y, int z, C own, C (&s)[3]) {
     C gx = (C)0, gy = (C)0, gz = (C)0;
 #define LBM_FM(I)                                                           \
     {                                                                       \
-        const C t = field_nbr<C, I>(v, b, q, x, y, z, own) * (C)w_of(I);    \
+        const C t = field_nbr<C, I, NC>(v, b, q, x, y, z, own) * (C)w_of(I); \
         if (cx_of(I)) gx += (C)cx_of(I) * t;                                \
         if (cy_of(I)) gy += (C)cy_of(I) * t;                                \
         if (cz_of(I)) gz += (C)cz_of(I) * t;                                \

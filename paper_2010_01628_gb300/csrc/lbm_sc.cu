@@ -17,44 +17,11 @@
 // the post-collision rest population is set from the mass balance
 // (conserve_mass): without it FP32 repeats the same rounding error at every
 // node of a uniform phase and loses about 2e-8 of density per node and step.
-#include "lbm_fluid.cuh"
 #include "lbm_internal.h"
 #include "lbm_reduce.cuh"
+#include "lbm_sc.cuh"
 
 namespace lbm {
-
-struct ScArgs {
-    Box box;
-    double omega, G;
-    double g[3];
-    double rg[3];  // rho_ref g: F = rho g - rho_ref g + F_sc
-    double lid[3];
-};
-
-template <typename C>
-__device__ __forceinline__ C pseudopotential(C rho) {
-    return (C)1 - exp(-rho);
-}
-
-// rho, F = rho g + F_sc and u = (j + F/2)/rho of a pulled node.
-template <typename C>
-__device__ __forceinline__ Macro<C> sc_macro(const Moments<C>& m, const C* __restrict__ psi, const Box& b,
-                                             const Nbr& q, int x, int y, int z, uint32_t self, const ScArgs& p) {
-    Macro<C> a;
-    a.rho = (C)1 + m.drho;
-    const C own = psi[self];
-    C s[3];
-    lattice_first_moment<C>(psi, b, q, x, y, z, own, s);
-    const C mg = -(C)p.G * own;
-    a.Fx = (a.rho * (C)p.g[0] - (C)p.rg[0]) + mg * s[0];
-    a.Fy = (a.rho * (C)p.g[1] - (C)p.rg[1]) + mg * s[1];
-    a.Fz = (a.rho * (C)p.g[2] - (C)p.rg[2]) + mg * s[2];
-    const C inv = recip(a.rho);
-    a.ux = (m.jx + (C)0.5 * a.Fx) * inv;
-    a.uy = (m.jy + (C)0.5 * a.Fy) * inv;
-    a.uz = (m.jz + (C)0.5 * a.Fz) * inv;
-    return a;
-}
 
 template <typename S, typename C, bool WALLS>
 __global__ void __launch_bounds__(256) sc_psi_kernel(const S* __restrict__ src, C* __restrict__ psi, ScArgs p) {

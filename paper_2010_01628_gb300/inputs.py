@@ -219,6 +219,15 @@ def droplet_sweep(ndomains=64, seed=5, sizes=(32, 48, 64, 96), ratio_range=(2.0,
     return [(int(a), float(b)) for a, b in zip(n, ratio)]
 
 
+def bubble_sweep(ndomains=64, seed=6, sizes=(32, 48, 64, 96), g_range=(-5.5, -4.5)):
+    """Shan-Chen sweep: (n_d, G_d) pairs; box d holds a centred static bubble
+    (static_bubble, sharp 1.95 / 0.15 start) of radius n_d / 4."""
+    rng = np.random.default_rng(seed)
+    n = rng.choice(np.array(sizes), size=ndomains)
+    G = rng.uniform(g_range[0], g_range[1], size=ndomains)
+    return [(int(a), float(b)) for a, b in zip(n, G)]
+
+
 def sweep_droplets(n, ratio, index, seed=5):
     """Fields (rho, u, phase) of domain `index` of droplet_sweep."""
     rho, u, phase, _, _ = droplets(n, seed=seed + index, r_min=max(4.0, n / 16.0), r_max=max(6.0, n / 8.0),
