@@ -273,11 +273,12 @@ lbm_status lbm_get_launch_shape(const lbm_ctx *ctx, int *variant, int *threads, 
  * fields) so that it iterates to the steady residual from there instead of
  * from rest.  The network is an addition of this library (the paper has no
  * learned component): 4 layers of 3x3x3 zero-padded convolutions,
- * 5 -> 32 -> 32 -> 32 -> 4 channels, ReLU after the first three, BF16
+ * 16 -> 32 -> 32 -> 32 -> 4 channels, ReLU after the first three, BF16
  * activations and kernel weights on the tensor cores, FP32 master weights,
  * gradients and Adam moments.
- * Inputs per node: (Re - 550)/450, the node-centre coordinates scaled to
- * [-1, 1], and 1 on the top (+y, lid) layer of nodes.  Outputs per node:
+ * Inputs per node (16): r = (Re - 550)/450, the node-centre coordinates
+ * x, y, z scaled to [-1, 1], 1 on the top (+y, lid) layer of nodes,
+ * cos(pi v/2), sin(pi v), cos(pi v) of each coordinate v, r^2, r (y + 1)/2.  Outputs per node:
  * (rho - 1) * 30 and u * 10 (lid speed 0.1 -> 1).
  * Parameters (lbm_cnn_param_count of them): per layer, weights
  * [C_out][C_in][27] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)) then biases [C_out].
@@ -292,7 +293,7 @@ lbm_status lbm_cnn_set_weights(lbm_cnn *net, const float *w, size_t count);
 lbm_status lbm_cnn_get_weights(lbm_cnn *net, float *w, size_t count);
 /* Input channels from the Reynolds number (device-side). */
 lbm_status lbm_cnn_set_input(lbm_cnn *net, double reynolds);
-/* Input channels given explicitly: x [n][5] FP32 (tests). */
+/* Input channels given explicitly: x [n][16] FP32 (tests). */
 lbm_status lbm_cnn_set_input_raw(lbm_cnn *net, const float *x, size_t count);
 /* Forward pass; out (optional) receives the [n][4] FP32 outputs. */
 lbm_status lbm_cnn_forward(lbm_cnn *net, float *out, size_t count);

@@ -1,7 +1,7 @@
 """FP64 numpy oracle of the warm-start network (test infrastructure only).
 
 Architecture: 4 layers of 3x3x3 zero-padded convolutions, channels
-5 -> 32 -> 32 -> 32 -> 4, ReLU after the first three.  Volume layout
+16 -> 32 -> 32 -> 32 -> 4, ReLU after the first three.  Volume layout
 [nz, ny, nx, channels] (node p = x + nx (y + ny z)); weights per layer
 [C_out, C_in, 27] with tap = (dz+1)*9 + (dy+1)*3 + (dx+1), then biases [C_out];
 all layers' parameters back to back.
@@ -15,7 +15,7 @@ finite-difference check of the analytic gradient.
 """
 import numpy as np
 
-CH = [5, 32, 32, 32, 4]
+CH = [16, 32, 32, 32, 4]
 RHO_SCALE, U_SCALE = 30.0, 10.0
 
 
@@ -107,14 +107,24 @@ def loss_and_grad(params, X0, rho, u):
 
 
 def features(shape, reynolds):
-    """Input channels of the library: (Re - 550)/450, node-centre coordinates
-    in [-1, 1], lid flag on the top (+y) layer; shape = (nx, ny, nz)."""
+    """Input channels of the library, shape = (nx, ny, nz): r = (Re - 550)/450;
+    node-centre coordinates x, y, z in [-1, 1]; lid flag on the top (+y)
+    layer; cos(pi x/2), cos(pi y/2), cos(pi z/2); sin(pi x), sin(pi y),
+    sin(pi z); cos(pi x), cos(pi y), cos(pi z); r^2; r (y + 1)/2."""
     nx, ny, nz = shape
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    f = np.zeros((nz, ny, nx, 5))
-    f[..., 0] = (reynolds - 550.0) / 450.0
-    f[..., 1] = 2.0 * (x + 0.5) / nx - 1.0
-    f[..., 2] = 2.0 * (y + 0.5) / ny - 1.0
-    f[..., 3] = 2.0 * (z + 0.5) / nz - 1.0
+    xn = 2.0 * (x + 0.5) / nx - 1.0
+    yn = 2.0 * (y + 0.5) / ny - 1.0
+    zn = 2.0 * (z + 0.5) / nz - 1.0
+    r = (reynolds - 550.0) / 450.0
+    f = np.zeros((nz, ny, nx, 16))
+    f[..., 0] = r
+    f[..., 1], f[..., 2], f[..., 3] = xn, yn, zn
     f[..., 4] = (y == ny - 1).astype(np.float64)
+    for k, v in enumerate((xn, yn, zn)):
+        f[..., 5 + k] = np.cos(0.5 * np.pi * v)
+        f[..., 8 + k] = np.sin(np.pi * v)
+        f[..., 11 + k] = np.cos(np.pi * v)
+    f[..., 14] = r * r
+    f[..., 15] = r * 0.5 * (yn + 1.0)
     return f

@@ -4,7 +4,7 @@
 // prediction initialises the populations (f = f_eq of the predicted fields).
 //
 // Architecture (fixed): 4 layers of 3x3x3 convolutions with zero padding,
-// 5 -> 32 -> 32 -> 32 -> 4 channels, ReLU after the first three.  Activations
+// 16 -> 32 -> 32 -> 32 -> 4 channels, ReLU after the first three.  Activations
 // and the weights used by the kernels are BF16 (channel-last, channels padded
 // to multiples of 16); master weights, gradients and Adam moments are FP32.
 //
@@ -34,10 +34,10 @@
 namespace cnn {
 
 constexpr int NL = 4;
-constexpr int C_IN_REAL = 5, C_OUT_REAL = 4;
+constexpr int C_IN_REAL = 16, C_OUT_REAL = 4;
 // padded channel counts per layer boundary: input 16, hidden 32, output 16
 constexpr int CH[NL + 1] = {16, 32, 32, 32, 16};
-constexpr int CH_REAL[NL + 1] = {5, 32, 32, 32, 4};
+constexpr int CH_REAL[NL + 1] = {16, 32, 32, 32, 4};
 constexpr float RHO_SCALE = 30.f;  // network output 0 = (rho - 1) * RHO_SCALE
 constexpr float U_SCALE = 10.f;    // outputs 1..3 = u * U_SCALE (lid speed 0.1 -> 1)
 
@@ -592,19 +592,36 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
     w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
 }
 
-// Input channels: [Re_n, x_n, y_n, z_n, lid] (+ zero padding to 16);
-// Re_n = (Re - 550)/450, coordinates of node centres scaled to [-1, 1], lid = 1
-// on the top (+y) layer of nodes.
+// Input channels (16): r = (Re - 550)/450; the node-centre coordinates
+// x, y, z scaled to [-1, 1]; lid = 1 on the top (+y) layer of nodes;
+// cos(pi x/2), cos(pi y/2), cos(pi z/2) (vanishing at the walls);
+// sin(pi x), sin(pi y), sin(pi z); cos(pi x), cos(pi y), cos(pi z); r^2;
+// r (y + 1)/2.  The smooth coordinate functions let four 3x3x3 layers (a
+// receptive field of 9 nodes) shape fields across the whole cavity.
 __global__ void features(__nv_bfloat16* __restrict__ X0, Shape s, float re_n) {
     const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.P) return;
     const int x = (int)(p % s.nx), y = (int)((p / s.nx) % s.ny), z = (int)(p / ((long)s.nx * s.ny));
-    float f[16] = {0};
+    float f[16];
+    const float xn = 2.f * (x + 0.5f) / s.nx - 1.f;
+    const float yn = 2.f * (y + 0.5f) / s.ny - 1.f;
+    const float zn = 2.f * (z + 0.5f) / s.nz - 1.f;
     f[0] = re_n;
-    f[1] = 2.f * (x + 0.5f) / s.nx - 1.f;
-    f[2] = 2.f * (y + 0.5f) / s.ny - 1.f;
-    f[3] = 2.f * (z + 0.5f) / s.nz - 1.f;
+    f[1] = xn;
+    f[2] = yn;
+    f[3] = zn;
     f[4] = y == s.ny - 1 ? 1.f : 0.f;
+    f[5] = cospif(0.5f * xn);
+    f[6] = cospif(0.5f * yn);
+    f[7] = cospif(0.5f * zn);
+    f[8] = sinpif(xn);
+    f[9] = sinpif(yn);
+    f[10] = sinpif(zn);
+    f[11] = cospif(xn);
+    f[12] = cospif(yn);
+    f[13] = cospif(zn);
+    f[14] = re_n * re_n;
+    f[15] = re_n * 0.5f * (yn + 1.f);
     uint32_t* o = reinterpret_cast<uint32_t*>(X0) + p * 8;
 #pragma unroll
     for (int k = 0; k < 8; ++k) o[k] = bf_pack(f[2 * k], f[2 * k + 1]);
@@ -1065,7 +1082,7 @@ lbm_status lbm_cnn_set_input(lbm_cnn* c, double reynolds) {
 }
 
 lbm_status lbm_cnn_set_input_raw(lbm_cnn* c, const float* x, size_t count) {
-    // x: [P][5] FP32 input channels (host or device); padded to BF16 [P][16]
+    // x: [P][16] FP32 input channels (host or device), stored as BF16 [P][16]
     if (!c || !x || count != (size_t)c->s.P * cnn::C_IN_REAL) return LBM_ERR_ARG;
     std::vector<float> h((size_t)c->s.P * 16, 0.f);
     std::vector<float> in(count);
@@ -1073,7 +1090,7 @@ lbm_status lbm_cnn_set_input_raw(lbm_cnn* c, const float* x, size_t count) {
     if (e != cudaSuccess) return cnn_cuda_fail(c, e, "lbm_cnn_set_input_raw");
     std::vector<__nv_bfloat16> hb((size_t)c->s.P * 16);
     for (long p = 0; p < c->s.P; ++p)
-        for (int k = 0; k < 16; ++k) hb[p * 16 + k] = __float2bfloat16_rn(k < 5 ? in[p * 5 + k] : 0.f);
+        for (int k = 0; k < 16; ++k) hb[p * 16 + k] = __float2bfloat16_rn(in[p * cnn::C_IN_REAL + k]);
     e = cudaMemcpyAsync(c->act[0], hb.data(), hb.size() * 2, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? LBM_OK : cnn_cuda_fail(c, e, "lbm_cnn_set_input_raw");

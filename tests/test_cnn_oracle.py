@@ -65,7 +65,13 @@ def test_gradient_matches_finite_differences():
 
 def test_features_layout():
     f = C.features((4, 3, 2), 1000.0)
-    assert f.shape == (2, 3, 4, 5)
-    assert np.allclose(f[..., 0], 1.0)
+    assert f.shape == (2, 3, 4, 16)
+    assert np.allclose(f[..., 0], 1.0) and np.allclose(f[..., 14], 1.0)
     assert f[0, 0, 0, 1] == -0.75 and f[0, 0, 3, 1] == 0.75
     assert np.all(f[:, 2, :, 4] == 1) and np.all(f[:, :2, :, 4] == 0)
+    # the wall-vanishing and periodic coordinate functions at x = -0.75
+    assert abs(f[0, 0, 0, 5] - np.cos(-0.375 * np.pi)) < 1e-15
+    assert abs(f[0, 0, 0, 8] - np.sin(-0.75 * np.pi)) < 1e-15
+    assert abs(f[0, 0, 0, 11] - np.cos(-0.75 * np.pi)) < 1e-15
+    # r (y + 1)/2: r at the top node centre y = 2/3
+    assert abs(f[0, 2, 0, 15] - 1.0 * (2.0 / 3.0 + 1.0) / 2.0) < 1e-15

@@ -35,10 +35,10 @@ def test_forward_matches_oracle(shape):
     from paper_2010_01628_gb300 import binding as L
     nx, ny, nz = shape
     p = params(1)
-    x = np.random.default_rng(2).uniform(-1, 1, (nz, ny, nx, 5))
+    x = np.random.default_rng(2).uniform(-1, 1, (nz, ny, nx, C.CH[0]))
     net = L.lbm_cnn_create(shape, p)
     try:
-        L.lbm_cnn_set_input_raw(net, x.reshape(-1, 5))
+        L.lbm_cnn_set_input_raw(net, x.reshape(-1, C.CH[0]))
         got = L.lbm_cnn_forward(net, nx * ny * nz)
     finally:
         L.lbm_cnn_destroy(net)
