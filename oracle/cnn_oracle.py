@@ -16,6 +16,7 @@ finite-difference check of the analytic gradient.
 import numpy as np
 
 CH = [16, 32, 32, 32, 4]
+NL = len(CH) - 1
 RHO_SCALE, U_SCALE = 30.0, 10.0
 
 
@@ -25,7 +26,7 @@ def taps():
 
 
 def layer_sizes():
-    return [27 * CH[l + 1] * CH[l] + CH[l + 1] for l in range(4)]
+    return [27 * CH[l + 1] * CH[l] + CH[l + 1] for l in range(NL)]
 
 
 def param_count():
@@ -34,7 +35,7 @@ def param_count():
 
 def split(params):
     out, o = [], 0
-    for l in range(4):
+    for l in range(NL):
         nw = 27 * CH[l + 1] * CH[l]
         W = params[o:o + nw].reshape(CH[l + 1], CH[l], 27)
         b = params[o + nw:o + nw + CH[l + 1]]
@@ -64,7 +65,7 @@ def forward(params, X0):
     x = X0
     for l, (W, b) in enumerate(split(params)):
         y = conv(x, W, b)
-        if l < 3:
+        if l < NL - 1:
             y = np.maximum(y, 0.0)
         acts.append(y)
         x = y
@@ -85,7 +86,7 @@ def loss_and_grad(params, X0, rho, u):
     dY = 2.0 * (Y - T) / n
     grads = []
     layers = split(params)
-    for l in range(3, -1, -1):
+    for l in range(NL - 1, -1, -1):
         W, b = layers[l]
         X = acts[l]
         shape = X.shape[:3]
