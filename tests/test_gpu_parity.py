@@ -18,12 +18,21 @@ from paper_2010_01628_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-3, "bf16": 4e-3}
+# The density deviation rho - 1 against its own norm: rho ~ 1 makes the plain
+# relative error of rho weak.  rho - 1 is 1e-3 to 1e-2 of rho on these cases,
+# so an error at the rho bound is 1e2 to 1e3 times larger relative to rho - 1;
+# the bounds sit between (measured on the GB300: FP64 <= 3e-11, FP32 <= 8e-5,
+# FP16 <= 5e-3, BF16 <= 6e-2).
+DRHO_TOL = {1e-12: 1e-10, 1e-5: 2e-4, 1e-3: 2e-2, 4e-3: 1e-1}
 
 
 def compare(g, o, tol, fields=("rho", "u")):
     errs = {k: rel_l2(g[k], o[k]) for k in fields}
-    for k, e in errs.items():
-        assert e <= tol, (k, errs)
+    errs["drho"] = rel_l2(g["rho"] - 1.0, o["rho"] - 1.0)
+    for k in fields:
+        assert errs[k] <= tol, (k, errs)
+    if tol in DRHO_TOL:
+        assert errs["drho"] <= DRHO_TOL[tol], ("drho", errs)
     return errs
 
 
