@@ -327,33 +327,55 @@ __device__ __forceinline__ void conserve_mass(C (&f)[Q], C drho) {
 }
 
 // f = M^-1 r (App. C, Eq. pdfQ19): populations from the 19 raw moments.
+// Each axis pair shares its common part (f_-/+ = E +- D) and each group of four
+// diagonal directions its sums and differences (f4, f5, f13, f14 =
+// (P +- D)/4, (P' +- S)/4 with P = r16 - r11, P' = r16 + r11, D = r7 - r10,
+// S = r7 + r10): fewer operations for the FP64 pipe, which bounds the FP64
+// step, and for the issue-bound colour-gradient collision.
 template <typename C>
 __device__ __forceinline__ void raw_to_populations(const C (&r)[Q], C (&f)[Q]) {
-    const C half = (C)0.5, quarter = (C)0.25, sixth = (C)(1.0 / 6.0);
+    const C half = (C)0.5, mhalf = (C)-0.5, quarter = (C)0.25, mquarter = (C)-0.25, sixth = (C)(1.0 / 6.0);
     const C ax = (r[4] + (C)2 * r[5] + r[6]) * sixth;
     const C ay = (r[4] - r[5] + r[6]) * sixth;
     const C az = (r[4] - r[5] - (C)2 * r[6]) * sixth;
     const C s1617 = r[16] + r[17], s1618 = r[16] + r[18], s1718 = r[17] + r[18];
     f[0] = r[0] - r[4] + r[16] + s1718;
-    const C bx = (r[11] + r[13]) * half, by = (r[10] + r[15]) * half, bz = (r[12] + r[14]) * half;
-    f[1] = bx - (r[1] + s1617) * half + ax;
-    f[10] = -bx + (r[1] - s1617) * half + ax;
-    f[2] = by - (r[2] + s1618) * half + ay;
-    f[11] = -by + (r[2] - s1618) * half + ay;
-    f[3] = bz - (r[3] + s1718) * half + az;
-    f[12] = -bz + (r[3] - s1718) * half + az;
-    f[4] = (r[7] + r[16] - r[10] - r[11]) * quarter;
-    f[5] = (r[10] + r[16] - r[7] - r[11]) * quarter;
-    f[13] = (r[7] + r[10] + r[11] + r[16]) * quarter;
-    f[14] = (r[11] + r[16] - r[7] - r[10]) * quarter;
-    f[6] = (r[8] + r[17] - r[12] - r[13]) * quarter;
-    f[7] = (r[12] + r[17] - r[8] - r[13]) * quarter;
-    f[15] = (r[8] + r[12] + r[13] + r[17]) * quarter;
-    f[16] = (r[13] + r[17] - r[8] - r[12]) * quarter;
-    f[8] = (r[9] + r[18] - r[14] - r[15]) * quarter;
-    f[9] = (r[14] + r[18] - r[9] - r[15]) * quarter;
-    f[17] = (r[9] + r[14] + r[15] + r[18]) * quarter;
-    f[18] = (r[15] + r[18] - r[9] - r[14]) * quarter;
+    {
+        const C e = s1617 * mhalf + ax, d = (r[11] + r[13] - r[1]) * half;
+        f[1] = e + d;
+        f[10] = e - d;
+    }
+    {
+        const C e = s1618 * mhalf + ay, d = (r[10] + r[15] - r[2]) * half;
+        f[2] = e + d;
+        f[11] = e - d;
+    }
+    {
+        const C e = s1718 * mhalf + az, d = (r[12] + r[14] - r[3]) * half;
+        f[3] = e + d;
+        f[12] = e - d;
+    }
+    {
+        const C pm = (r[16] - r[11]) * quarter, pp = (r[16] + r[11]) * quarter, dm = r[7] - r[10], dp = r[7] + r[10];
+        f[4] = dm * quarter + pm;
+        f[5] = dm * mquarter + pm;
+        f[13] = dp * quarter + pp;
+        f[14] = dp * mquarter + pp;
+    }
+    {
+        const C pm = (r[17] - r[13]) * quarter, pp = (r[17] + r[13]) * quarter, dm = r[8] - r[12], dp = r[8] + r[12];
+        f[6] = dm * quarter + pm;
+        f[7] = dm * mquarter + pm;
+        f[15] = dp * quarter + pp;
+        f[16] = dp * mquarter + pp;
+    }
+    {
+        const C pm = (r[18] - r[15]) * quarter, pp = (r[18] + r[15]) * quarter, dm = r[9] - r[14], dp = r[9] + r[14];
+        f[8] = dm * quarter + pm;
+        f[9] = dm * mquarter + pm;
+        f[17] = dp * quarter + pp;
+        f[18] = dp * mquarter + pp;
+    }
 }
 
 // raw_to_populations with the result in the 16-bit formats' units,

@@ -272,7 +272,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, const char* cache_path, int force
             int variant, threads, stages, ctas;
         };
         std::vector<Cand> cands;
-        for (int bx : {64, 128, 256}) cands.push_back({0, bx, 0, 1});
+        for (int bx : {32, 64, 128, 256}) cands.push_back({0, bx, 0, 1});  // 32: small grids over all SMs
         if (lbm::packed16_ok(c)) {
             if (c->box.nx % 2 == 0)
                 for (int bx : {128, 256}) cands.push_back({2, bx, 0, 1});
