@@ -285,7 +285,7 @@ def _cnn(L, torch, timed, n=128, steps=20):
         "train_step_ms": t_train * 1e3, "train_TFLOPs": tf_train, "train_frac_of_bf16_sustained": tf_train / sustained,
         "forward_ms": t_fwd * 1e3, "forward_TFLOPs": tf_fwd, "forward_frac_of_bf16_burst": tf_fwd / burst,
         "peak_kind": kind, "steps": steps,
-        "note": "tcgen05 BF16 MMAs (TMEM accumulators, tensor-map TMA staging); FLOPs with padded channels "
+        "note": "tcgen05 BF16 MMAs (TMEM accumulators, bulk-copy row staging); FLOPs with padded channels "
                 "16-32-32-32-16; the train step includes the loss, Adam and weight packing; each call synchronises"}}
 
 

@@ -7,17 +7,24 @@
 // 16 -> 32 -> 32 -> 32 -> 4 channels, ReLU after the first three (six layers
 // predicted u slightly better, 0.050 against 0.054, but warm-started the
 // solver less well: 55 % against 59 % mean wall-time reduction).  Activations
-// and the weights used by the kernels are BF16 (channel-last, channels padded
-// to multiples of 16); master weights, gradients and Adam moments are FP32.
+// and the weights used by the kernels are BF16, master weights, gradients and
+// Adam moments FP32.  Activations are stored channel-chunked,
+// [C/8][z][y][x][8] (8 channels = 16 bytes per node and chunk plane).
 //
 // Kernels:
 //  - conv_tc: implicit GEMM on the tensor cores: tcgen05.mma (BF16 operands,
-//    FP32 accumulators in TMEM) fed by tensor-map TMA copies of the 27 shifted
-//    128-voxel boxes; the same kernel runs the backward data pass with the
-//    flipped, transposed weights.
-//  - wgrad_tc: weight gradients on the tensor cores (taps x input channels as
-//    M, output channels as N, voxels as K), one partial per CTA summed in a
-//    fixed order; bias_grad: bias gradients.
+//    FP32 accumulators in TMEM).  A tile is a 128-node segment of an x-row;
+//    per (dy, dz) the 130-node row (with its x-halo) of every channel chunk
+//    is staged by 1D bulk copies of its contiguous runs, and the three
+//    x-shifted taps read it through descriptor start offsets of 16 bytes
+//    (unswizzled core matrices): 9 staged rows per tile instead of 27 boxes.
+//    The same kernel runs the backward data pass with the flipped, transposed
+//    weights.
+//  - wgrad_tc: weight gradients on the tensor cores (rows x input channels as
+//    M at one x-shift, output channels as N, voxels as K) from the same nine
+//    staged rows per tile, with the bias gradients summed from the staged dY
+//    tiles by the otherwise idle epilogue warps; one partial per CTA, summed
+//    in a fixed order.
 //  - adam: the optimiser step on the FP32 master weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -69,38 +76,49 @@ __device__ __forceinline__ uint32_t bf_pack(float a, float b) {
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core convolution (tcgen05, TMEM accumulators, TMA operand staging).
+// Tensor-core convolution (tcgen05, TMEM accumulators, bulk-copy staging).
 //
-// Implicit GEMM per tile of 128 voxels: D[voxel][co] = sum over the 27 taps of
-// A_tap[voxel][ci] W[tap][co][ci].  A tile is a box of BX x BY x BZ = 128
-// voxels; A_tap is the same box shifted by the tap's offset, loaded by a 4D
-// tensor-map copy whose out-of-range elements are zero (the convolution's zero
-// padding).  Rows of A and W are K-major (channels contiguous) in the TMA's
-// 64-byte (CI = 32) or 32-byte (CI = 16) swizzle.  The 27 weight taps stay in
-// shared memory for the CTA's life.
+// Implicit GEMM per tile of 128 voxels, a segment x0 .. x0 + 127 of the x-row
+// (y, z): D[x][co] = sum over the 27 taps of A_tap[x][ci] W[tap][co][ci].
+// For each (dy, dz) the row (y + dy, z + dz), nodes x0 - 1 .. x0 + 128 of
+// every channel chunk, is staged as [chunk][130 cells][8 channels]: in the
+// channel-chunked activation layout each chunk's run of the row is contiguous
+// in memory, so one 1D bulk copy per chunk moves it whole (full 128-byte
+// lines, where a tensor-map box with 16-byte rows moved 32-byte sectors half
+// used).  Cells outside the grid are zeros written by the producer warp (the
+// x-halo cells at the two ends; whole rows outside in y or z), which is the
+// convolution's zero padding.  In that layout a K-major operand is a run of
+// unswizzled core matrices (8 nodes x 16 bytes, contiguous), so the tap dx
+// reads the same row from a start 16 (dx + 1) bytes on (leading offset = the
+// chunk stride, stride offset = 128 bytes).  The weights are K-major in the
+// TMA's 64-byte (CI = 32) or 32-byte (CI = 16) swizzle and stay in shared
+// memory for the CTA's life.
 //
-// Roles (192 threads): warp 0 lane 0 issues the TMA copies into a ring of
-// NSTAGE A buffers; warp 1 allocates TMEM and its lane 0 issues the MMAs
-// (M = 128, N = CO, K = 16) into one of two TMEM accumulators; warps 2-5 read
-// the finished accumulator (each warp its 32-lane quarter: one voxel per
-// thread, CO columns), apply the epilogue and store.  Every wait is bounded
-// (TC_WAIT_NS); on expiry the kernel records LBM_ERR_TIMEOUT in *status, the
-// other roles stop, the copies and MMAs in flight are drained (bounded) and
-// TMEM is freed.
+// Roles (192 threads): warp 0 stages rows into a ring of NSTAGE buffers (lane
+// 0 waits and issues the copies, the warp writes the zero cells); warp 1
+// allocates TMEM and its lane 0 issues the MMAs (M = 128, N = CO, K = 16) into
+// one of two TMEM accumulators; warps 2-5 read the finished accumulator (each
+// warp its 32-lane quarter: one voxel per thread, CO columns), apply the
+// epilogue and store.  Every wait is bounded (TC_WAIT_NS); on expiry the
+// kernel records LBM_ERR_TIMEOUT in *status, the other roles stop, the copies
+// and MMAs in flight are drained (bounded) and TMEM is freed.
 constexpr int TILE_M = 128;
+constexpr int ROW_NODES = TILE_M + 2;       // a staged row: the tile and its x-halo
+constexpr int ROW_CHUNK = ROW_NODES * 16;  // one channel chunk of a staged row (bytes)
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;
 
+// Tiles are 128-node segments of x-rows: ntx segments per row, ny * nz rows.
 struct TileGeom {
-    int nx, ny, nz;     // grid
-    int bx, by, bz;     // box of one tile (bx * by * bz = 128)
-    int ntx, nty, ntz;  // tiles per axis
+    int nx, ny, nz;
+    int ntx;
     int ntiles;
+    long P;  // nodes (chunk-plane stride)
 };
 
 __device__ __forceinline__ void tile_origin(const TileGeom& g, int t, int& x0, int& y0, int& z0) {
-    x0 = (t % g.ntx) * g.bx;
-    y0 = ((t / g.ntx) % g.nty) * g.by;
-    z0 = (t / (g.ntx * g.nty)) * g.bz;
+    x0 = (t % g.ntx) * TILE_M;
+    y0 = (t / g.ntx) % g.ny;
+    z0 = t / (g.ntx * g.ny);
 }
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
@@ -127,27 +145,82 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
 __device__ __forceinline__ void tc_drain(uint64_t* bar, uint32_t parity) {
     lbm::mbar_wait_bounded(bar, parity, TC_WAIT_NS);
 }
+// Lane 0 waits, the warp learns the outcome.
+__device__ __forceinline__ bool tc_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                             int lane) {
+    bool ok = false;
+    if (lane == 0) ok = tc_wait(bar, parity, abort_flag, status);
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// The in-grid run of a staged row: cells c0 .. c0 + n - 1 of 0 .. 129 hold
+// nodes x0 - 1 + cell of row (y, z), starting at node index `src`; n = 0 when
+// the row lies outside the grid in y or z.
+struct RowRun {
+    int c0, n;
+    long src;
+};
+
+__device__ __forceinline__ RowRun row_run(const TileGeom& g, int x0, int y, int z) {
+    RowRun r{0, 0, 0};
+    if (y < 0 || y >= g.ny || z < 0 || z >= g.nz) return r;
+    const int xa = max(x0 - 1, 0), xb = min(x0 + TILE_M + 1, g.nx);
+    r.c0 = xa - (x0 - 1);
+    r.n = xb - xa;
+    r.src = ((long)z * g.ny + y) * g.nx + xa;
+    return r;
+}
+
+// Warp-wide: write the zero cells of a staged row of NCH chunks (all of it
+// when it lies outside the grid; else the x-halo cell before the run when x0 =
+// 0 and the cell after it when the run ends at the grid's edge).  Cells
+// further right only feed nodes beyond the edge, whose outputs are discarded
+// (convolution) or whose gradient is zero (weight gradient).  Generic stores,
+// made visible to the tensor cores' async proxy by the fence the caller runs.
+template <int NCH>
+__device__ __forceinline__ void zero_row_cells(uint8_t* slot, const RowRun& r, int lane) {
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (r.n == 0) {
+        for (int i = lane; i < NCH * ROW_NODES; i += 32) reinterpret_cast<uint4*>(slot)[i] = z;
+        return;
+    }
+    if (lane < NCH) {
+        if (r.c0 > 0) reinterpret_cast<uint4*>(slot + lane * ROW_CHUNK)[0] = z;
+        if (r.c0 + r.n < ROW_NODES) reinterpret_cast<uint4*>(slot + lane * ROW_CHUNK)[r.c0 + r.n] = z;
+    }
+}
+
+// Lane 0: the bulk copies of a staged row's in-grid run, one per chunk.
+template <int NCH>
+__device__ __forceinline__ void copy_row(uint8_t* slot, const __nv_bfloat16* X, long P, const RowRun& r,
+                                         uint64_t* bar) {
+    if (r.n == 0) return;
+    for (int c = 0; c < NCH; ++c)
+        lbm::bulk_g2s(slot + c * ROW_CHUNK + r.c0 * 16, X + ((size_t)c * P + r.src) * 8, (uint32_t)r.n * 16u, bar);
+}
 
 template <int CI, int CO, int NSTAGE>
 struct ConvLayout {
-    static constexpr int A_BYTES = TILE_M * CI * 2;
+    static constexpr int A_BYTES = (CI / 8) * ROW_CHUNK;          // a staged row, all chunks
+    static constexpr int A_STRIDE = (A_BYTES + 127) / 128 * 128;  // ring slots on 128-byte boundaries
     static constexpr int W_BYTES = 27 * CO * CI * 2;
     static constexpr int A_OFF = (W_BYTES + 1023) / 1024 * 1024;
-    static constexpr int BAR_OFF = A_OFF + NSTAGE * A_BYTES;
+    static constexpr int BAR_OFF = (A_OFF + NSTAGE * A_STRIDE + 7) / 8 * 8;
     static constexpr int NBAR = 2 * NSTAGE + 6;  // full, empty, tmem full x2, tmem empty x2, weights, drain
     static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 1024;  // + TMEM slot, abort flag, alignment slack
-    static constexpr uint32_t SWZ = CI == 32 ? tc::SW_64B : tc::SW_32B;
+    static constexpr uint32_t SWZ_W = CI == 32 ? tc::SW_64B : tc::SW_32B;
     static constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_M, CO, false, false);
-    static_assert(A_BYTES % 1024 == 0, "A stages must keep the swizzle alignment");
+    static_assert(A_OFF % 1024 == 0 && A_STRIDE % 128 == 0, "weights on the swizzle period, slots 128-byte aligned");
 };
 
 constexpr int CONV_STAGES = 6;
 
-// EPI: 0 = +bias, ReLU, BF16 out [P][CO]; 1 = +bias, FP32 out [P][CO];
-// 2 = zero where `gate` (this layer's forward activation) is not positive,
-// BF16 out, no bias.
+// EPI: 0 = +bias, ReLU, BF16 out (chunked); 1 = +bias, FP32 out [P][4] (the
+// output layer's real channels);
+// 2 = zero where `gate` (this layer's forward activation, chunked) is not
+// positive, BF16 out (chunked), no bias.
 template <int CI, int CO, int EPI>
-__global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorMap mapX,
+__global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__ X,
                                                const __grid_constant__ CUtensorMap mapW, const float* __restrict__ bias,
                                                void* __restrict__ Y, const __nv_bfloat16* __restrict__ gate,
                                                TileGeom g, int* status) {
@@ -190,12 +263,13 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
-    if (threadIdx.x == 0) {
-        // ---- TMA producer ----
-        tc::prefetch_map(&mapX);
-        tc::prefetch_map(&mapW);
-        lbm::mbar_arrive_expect_tx(wfull, Lay::W_BYTES);
-        tc::tma_load_3d(sW, &mapW, 0, 0, 0, wfull);
+    if (warp == 0) {
+        // ---- producer warp: 9 staged rows per tile ----
+        if (lane == 0) {
+            tc::prefetch_map(&mapW);
+            lbm::mbar_arrive_expect_tx(wfull, Lay::W_BYTES);
+            tc::tma_load_3d(sW, &mapW, 0, 0, 0, wfull);
+        }
         int armed[NSTAGE];
         for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
         int stage = 0;
@@ -204,28 +278,35 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
         for (int t = blockIdx.x; t < g.ntiles && ok; t += gridDim.x) {
             int x0, y0, z0;
             tile_origin(g, t, x0, y0, z0);
-            for (int tap = 0; tap < 27; ++tap) {
-                if (!tc_wait(&empty[stage], phase ^ 1u, abort_flag, status)) {
+            for (int r = 0; r < 9; ++r) {
+                if (!tc_wait_warp(&empty[stage], phase ^ 1u, abort_flag, status, lane)) {
                     ok = false;
                     break;
                 }
-                int dx, dy, dz;
-                tap_offset(tap, dx, dy, dz);
-                lbm::mbar_arrive_expect_tx(&full[stage], Lay::A_BYTES);
-                tc::tma_load_4d(sA + stage * Lay::A_BYTES, &mapX, 0, x0 + dx, y0 + dy, z0 + dz, &full[stage]);
-                armed[stage] = (int)phase;
+                const RowRun run = row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1);
+                uint8_t* slot = sA + stage * Lay::A_STRIDE;
+                zero_row_cells<CI / 8>(slot, run, lane);
+                lbm::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    lbm::mbar_arrive_expect_tx(&full[stage], (uint32_t)((CI / 8) * run.n * 16));
+                    copy_row<CI / 8>(slot, X, g.P, run, &full[stage]);
+                    armed[stage] = (int)phase;
+                }
                 if (++stage == NSTAGE) {
                     stage = 0;
                     phase ^= 1u;
                 }
             }
         }
-        // the copies land by themselves: wait for the last one of every stage
-        for (int s = 0; s < NSTAGE; ++s)
-            if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
-        tc_drain(wfull, 0);
+        if (lane == 0) {
+            // the copies land by themselves: wait for the last one of every stage
+            for (int s = 0; s < NSTAGE; ++s)
+                if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
+            tc_drain(wfull, 0);
+        }
     } else if (threadIdx.x == 32) {
-        // ---- MMA issuer ----
+        // ---- MMA issuer: three taps (dx = -1, 0, 1) per staged row ----
         if (tc_wait(wfull, 0, abort_flag, status)) {
             tc::fence_after_sync();
             int stage = 0;
@@ -238,17 +319,24 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
                 if (!tc_wait(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, abort_flag, status)) break;
                 tc::fence_after_sync();
                 const uint32_t d = tbase + (uint32_t)(acc * CO);
-                for (int tap = 0; tap < 27; ++tap) {
+                for (int r = 0; r < 9; ++r) {
                     if (!tc_wait(&full[stage], phase, abort_flag, status)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
+                    const uint32_t arow = a0 + stage * Lay::A_STRIDE;
 #pragma unroll
-                    for (int k = 0; k < CI / 16; ++k) {
-                        const uint64_t ad = tc::smem_desc(a0 + stage * Lay::A_BYTES + k * 32, 16, 8 * CI * 2, Lay::SWZ);
-                        const uint64_t bd = tc::smem_desc(w0 + tap * CO * CI * 2 + k * 32, 16, 8 * CI * 2, Lay::SWZ);
-                        tc::mma_bf16(d, ad, bd, Lay::IDESC, tap > 0 || k > 0);
+                    for (int dxi = 0; dxi < 3; ++dxi) {
+                        const int tap = r * 3 + dxi;  // (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+#pragma unroll
+                        for (int k = 0; k < CI / 16; ++k) {
+                            const uint64_t ad =
+                                tc::smem_desc(arow + dxi * 16 + k * 2 * ROW_CHUNK, ROW_CHUNK, 128, tc::SW_NONE);
+                            const uint64_t bd =
+                                tc::smem_desc(w0 + tap * CO * CI * 2 + k * 32, 16, 8 * CI * 2, Lay::SWZ_W);
+                            tc::mma_bf16(d, ad, bd, Lay::IDESC, r > 0 || dxi > 0 || k > 0);
+                        }
                     }
                     tc::mma_commit(&empty[stage]);
                     if (++stage == NSTAGE) {
@@ -271,10 +359,7 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
         int it = 0;
         for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x, ++it) {
             const int acc = it & 1;
-            bool ok = false;
-            if (lane == 0) ok = tc_wait(&tfull[acc], ((uint32_t)it >> 1) & 1u, abort_flag, status);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
+            if (!tc_wait_warp(&tfull[acc], ((uint32_t)it >> 1) & 1u, abort_flag, status, lane)) break;
             tc::fence_after_sync();
             uint32_t r[CO];
             if constexpr (CO == 32)
@@ -287,9 +372,9 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
             if (lane == 0) tc::mbar_arrive(&tempty[acc]);
             int x0, y0, z0;
             tile_origin(g, t, x0, y0, z0);
-            const int x = x0 + row % g.bx, y = y0 + (row / g.bx) % g.by, z = z0 + row / (g.bx * g.by);
-            if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
-            const long p = ((long)z * g.ny + y) * g.nx + x;
+            const int x = x0 + row;
+            if (x >= g.nx) continue;
+            const long p = ((long)z0 * g.ny + y0) * g.nx + x;
             float v[CO];
 #pragma unroll
             for (int co = 0; co < CO; ++co) v[co] = __uint_as_float(r[co]) + bvals[co];
@@ -298,10 +383,9 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
                 for (int co = 0; co < CO; ++co) v[co] = fmaxf(v[co], 0.f);
             }
             if (EPI == 2) {
-                const uint4* gp = reinterpret_cast<const uint4*>(gate) + p * (CO / 8);
 #pragma unroll
                 for (int j = 0; j < CO / 8; ++j) {
-                    const uint4 gw = __ldg(gp + j);
+                    const uint4 gw = __ldg(reinterpret_cast<const uint4*>(gate) + (size_t)j * g.P + p);
                     const uint32_t w4[4] = {gw.x, gw.y, gw.z, gw.w};
 #pragma unroll
                     for (int h = 0; h < 4; ++h) {
@@ -311,15 +395,13 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
                 }
             }
             if (EPI == 1) {
-                float4* yp = reinterpret_cast<float4*>(Y) + p * (CO / 4);
-#pragma unroll
-                for (int j = 0; j < CO / 4; ++j) yp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                reinterpret_cast<float4*>(Y)[p] = make_float4(v[0], v[1], v[2], v[3]);
             } else {
-                uint4* yp = reinterpret_cast<uint4*>(Y) + p * (CO / 8);
 #pragma unroll
                 for (int j = 0; j < CO / 8; ++j)
-                    yp[j] = make_uint4(bf_pack(v[8 * j], v[8 * j + 1]), bf_pack(v[8 * j + 2], v[8 * j + 3]),
-                                       bf_pack(v[8 * j + 4], v[8 * j + 5]), bf_pack(v[8 * j + 6], v[8 * j + 7]));
+                    reinterpret_cast<uint4*>(Y)[(size_t)j * g.P + p] =
+                        make_uint4(bf_pack(v[8 * j], v[8 * j + 1]), bf_pack(v[8 * j + 2], v[8 * j + 3]),
+                                   bf_pack(v[8 * j + 4], v[8 * j + 5]), bf_pack(v[8 * j + 6], v[8 * j + 7]));
             }
         }
     }
@@ -332,66 +414,76 @@ __global__ void __launch_bounds__(192) conv_tc(const __grid_constant__ CUtensorM
 }
 
 // Weight gradient on the tensor cores: dW[tap][co][ci] = sum_p dY[p][co]
-// X[p + off(tap)][ci], as D[(tap, ci)][co] = A[(tap, ci)][p] B[p][co] with
-// M = 128 = TG taps x CI channels per tap group (TG = 4 for CI = 32, 8 for
-// CI = 16; 7 or 4 groups, the last padded with a repeated tap whose rows are
-// discarded) and the voxels of a tile as K.  Both operands are MN-major (the
-// channels are contiguous in the staged boxes): the TG shifted X boxes of a
-// group sit back to back, so one descriptor spans them with the box size as
-// its leading (M) offset.  Every group accumulates in its own TMEM columns
-// over all tiles of the CTA's contiguous range; the epilogue writes one
-// partial per CTA, laid out [27][CO][CI], summed later in a fixed order.
+// X[p + off(tap)][ci].  Per tile (an x-row segment of 128 voxels) the nine
+// rows (y + dy, z + dz) of X are staged as for the convolution, back to back
+// ([row][chunk][130 cells][8 channels]), and the tile's dY as [chunk][128][8].
+// D[(row, ci)][co] = A[(row, ci)][p] B[p][co] with M = 128 = TG rows x CI
+// channels (TG = 4 for CI = 32, 8 for CI = 16) at one dx, the 128 voxels as
+// K: both operands are MN-major runs of unswizzled core matrices (8 voxels x 8
+// channels, 128 contiguous bytes), 8-voxel groups 128 bytes apart (leading
+// offset) and channel chunks one chunk stride apart (stride offset); the
+// chunks of consecutive staged rows continue at that stride, so one
+// descriptor spans TG rows, and the tap dx starts 16 (dx + 1) bytes on.  The
+// row groups start at rows 0, TG, ... with the last one moved back to end at
+// row 8 (its rows already covered are discarded).  Every (row group, dx)
+// accumulates in its own TMEM columns over all tiles of the CTA's contiguous
+// range; the epilogue writes one partial per CTA, laid out [27][CO][CI],
+// summed later in a fixed order.  The epilogue warps, idle until the end,
+// also sum each staged dY tile over its voxels (the bias gradient, one
+// partial per CTA beside the weights'), so a stage is free once the MMAs and
+// those four warps are done with it.  On a tile cut by the grid's x-edge only
+// the 16-voxel K-steps holding grid voxels are issued and dY is zeroed up to
+// the step's end; the ring is zeroed at start so that every staged value the
+// MMAs read is finite.
 template <int CI, int CO>
 struct WgLayout {
     static constexpr int TG = TILE_M / CI;
-    static constexpr int NG = (27 + TG - 1) / TG;
-    static constexpr int XB = TILE_M * CI * 2;
-    static constexpr int STAGE = TG * XB;
-    static constexpr int YB = TILE_M * CO * 2;
-    static constexpr int NSTAGE = 4;
-    static constexpr int Y_OFF = NSTAGE * STAGE;
-    static constexpr int BAR_OFF = Y_OFF + 2 * YB;
-    static constexpr int NBAR = 2 * NSTAGE + 4 + 2;  // full, empty, y full x2, y empty x2, acc full, drain
-    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 1024;
-    static constexpr int TCOLS_USED = NG * CO;
-    static constexpr uint32_t TCOLS = TCOLS_USED <= 32 ? 32 : (TCOLS_USED <= 64 ? 64 : (TCOLS_USED <= 128 ? 128 : 256));
-    static constexpr uint32_t SWX = CI == 32 ? tc::SW_64B : tc::SW_32B;
-    static constexpr uint32_t SWY = CO == 32 ? tc::SW_64B : tc::SW_32B;
+    static constexpr int NRG = (9 + TG - 1) / TG;  // row groups
+    static constexpr int NGRP = 3 * NRG;           // (row group, dx) accumulators
+    static constexpr int ROW = (CI / 8) * ROW_CHUNK;
+    static constexpr int XB = 9 * ROW;
+    static constexpr int YCHUNK = TILE_M * 16;
+    static constexpr int YB = (CO / 8) * YCHUNK;
+    static constexpr int STAGE = (XB + YB + 127) / 128 * 128;
+    static constexpr int NSTAGE = CI == 32 ? 2 : 4;
+    static constexpr int BAR_OFF = NSTAGE * STAGE;
+    static constexpr int NBAR = 2 * NSTAGE + 2;  // full, empty, acc full, drain
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 4 * CO * 4 + 1024;  // + TMEM slot, flag, bias sums
+    static constexpr int TCOLS_USED = NGRP * CO;
+    static constexpr uint32_t TCOLS =
+        TCOLS_USED <= 64 ? 64 : (TCOLS_USED <= 128 ? 128 : (TCOLS_USED <= 256 ? 256 : 512));
     static constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_M, CO, true, true);
-    static_assert(TG * CI == TILE_M && TCOLS_USED <= 256, "tap groups must fill M = 128 within 256 TMEM columns");
-    static_assert(XB % 1024 == 0 && YB % 1024 == 0, "boxes must keep the swizzle alignment");
+    static_assert(TG * CI == TILE_M && TCOLS_USED <= 512, "row groups must fill M = 128 within 512 TMEM columns");
+    static_assert(XB % 16 == 0 && BYTES <= 227 * 1024, "staging must fit shared memory");
+    __host__ __device__ static constexpr int group_row0(int rg) { return rg * TG < 9 - TG ? rg * TG : 9 - TG; }
 };
 
 template <int CI, int CO>
-__global__ void __launch_bounds__(192) wgrad_tc(const __grid_constant__ CUtensorMap mapX,
-                                                const __grid_constant__ CUtensorMap mapY, float* __restrict__ partial,
+__global__ void __launch_bounds__(192) wgrad_tc(const __nv_bfloat16* __restrict__ X,
+                                                const __nv_bfloat16* __restrict__ dY, float* __restrict__ partial,
                                                 TileGeom g, int* status) {
     using Lay = WgLayout<CI, CO>;
     constexpr int NSTAGE = Lay::NSTAGE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
-    uint8_t* sA = sm;
-    uint8_t* sY = sm + Lay::Y_OFF;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + Lay::BAR_OFF);
     uint64_t* empty = full + NSTAGE;
-    uint64_t* yfull = empty + NSTAGE;
-    uint64_t* yempty = yfull + 2;
-    uint64_t* accfull = yempty + 2;
+    uint64_t* accfull = empty + NSTAGE;
     uint64_t* drain = accfull + 1;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    float* sbias = reinterpret_cast<float*>(tslot + 4);  // [4 warps][CO]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = (g.ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
     const int t_begin = min(g.ntiles, (int)blockIdx.x * per), t_end = min(g.ntiles, t_begin + per);
 
+    for (int i = threadIdx.x; i < NSTAGE * Lay::STAGE / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    lbm::fence_proxy_async();
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             lbm::mbar_init(&full[s], 1);
-            lbm::mbar_init(&empty[s], 1);
-        }
-        for (int a = 0; a < 2; ++a) {
-            lbm::mbar_init(&yfull[a], 1);
-            lbm::mbar_init(&yempty[a], 1);
+            lbm::mbar_init(&empty[s], 5);  // the MMAs' commit and the four epilogue warps
         }
         lbm::mbar_init(accfull, 1);
         lbm::mbar_init(drain, 1);
@@ -407,98 +499,148 @@ __global__ void __launch_bounds__(192) wgrad_tc(const __grid_constant__ CUtensor
     tc::fence_after_sync();
     const uint32_t tbase = *tslot;
 
-    if (threadIdx.x == 0) {
-        // ---- TMA producer ----
-        tc::prefetch_map(&mapX);
-        tc::prefetch_map(&mapY);
-        int armed[NSTAGE], yarmed[2] = {-1, -1};
+    if (warp == 0) {
+        // ---- producer warp: the nine X rows and dY of each tile ----
+        int armed[NSTAGE];
         for (int s = 0; s < NSTAGE; ++s) armed[s] = -1;
         int stage = 0;
         uint32_t phase = 0;
-        bool ok = true;
-        for (int t = t_begin, it = 0; t < t_end && ok; ++t, ++it) {
+        for (int t = t_begin; t < t_end; ++t) {
+            if (!tc_wait_warp(&empty[stage], phase ^ 1u, abort_flag, status, lane)) break;
             int x0, y0, z0;
             tile_origin(g, t, x0, y0, z0);
-            const int ys = it & 1;
-            if (!tc_wait(&yempty[ys], (((uint32_t)it >> 1) & 1u) ^ 1u, abort_flag, status)) break;
-            lbm::mbar_arrive_expect_tx(&yfull[ys], Lay::YB);
-            tc::tma_load_4d(sY + ys * Lay::YB, &mapY, 0, x0, y0, z0, &yfull[ys]);
-            yarmed[ys] = (int)(((uint32_t)it >> 1) & 1u);
-            for (int gi = 0; gi < Lay::NG; ++gi) {
-                if (!tc_wait(&empty[stage], phase ^ 1u, abort_flag, status)) {
-                    ok = false;
-                    break;
-                }
-                lbm::mbar_arrive_expect_tx(&full[stage], Lay::STAGE);
-                for (int j = 0; j < Lay::TG; ++j) {
-                    const int tap = min(26, gi * Lay::TG + j);
-                    int dx, dy, dz;
-                    tap_offset(tap, dx, dy, dz);
-                    tc::tma_load_4d(sA + stage * Lay::STAGE + j * Lay::XB, &mapX, 0, x0 + dx, y0 + dy, z0 + dz,
-                                    &full[stage]);
-                }
+            uint8_t* sx = sm + stage * Lay::STAGE;
+            uint8_t* sy = sx + Lay::XB;
+            uint32_t bytes = 0;
+            for (int r = 0; r < 9; ++r) {
+                const RowRun run = row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1);
+                zero_row_cells<CI / 8>(sx + r * Lay::ROW, run, lane);
+                bytes += (uint32_t)((CI / 8) * run.n * 16);
+            }
+            const int nv = min(TILE_M, g.nx - x0);
+            const int kend = (nv + 15) / 16 * 16;
+            for (int i = lane; i < (CO / 8) * (kend - nv); i += 32)
+                reinterpret_cast<uint4*>(sy + (i / (kend - nv)) * Lay::YCHUNK)[nv + i % (kend - nv)] =
+                    make_uint4(0u, 0u, 0u, 0u);
+            lbm::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                lbm::mbar_arrive_expect_tx(&full[stage], bytes + (uint32_t)((CO / 8) * nv * 16));
+                for (int r = 0; r < 9; ++r)
+                    copy_row<CI / 8>(sx + r * Lay::ROW, X, g.P, row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1),
+                                     &full[stage]);
+                const long p0 = ((long)z0 * g.ny + y0) * g.nx + x0;
+                for (int c = 0; c < CO / 8; ++c)
+                    lbm::bulk_g2s(sy + c * Lay::YCHUNK, dY + ((size_t)c * g.P + p0) * 8, (uint32_t)nv * 16u,
+                                  &full[stage]);
                 armed[stage] = (int)phase;
-                if (++stage == NSTAGE) {
-                    stage = 0;
-                    phase ^= 1u;
-                }
+            }
+            if (++stage == NSTAGE) {
+                stage = 0;
+                phase ^= 1u;
             }
         }
-        for (int s = 0; s < NSTAGE; ++s)
-            if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
-        for (int s = 0; s < 2; ++s)
-            if (yarmed[s] >= 0) tc_drain(&yfull[s], (uint32_t)yarmed[s]);
+        if (lane == 0)
+            for (int s = 0; s < NSTAGE; ++s)
+                if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer ----
-        const uint32_t a0 = lbm::smem_u32(sA), y0s = lbm::smem_u32(sY);
+        const uint32_t s0 = lbm::smem_u32(sm);
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (int t = t_begin, it = 0; t < t_end && ok; ++t, ++it) {
-            const int ys = it & 1;
-            if (!tc_wait(&yfull[ys], ((uint32_t)it >> 1) & 1u, abort_flag, status)) {
+        for (int t = t_begin, it = 0; t < t_end; ++t, ++it) {
+            if (!tc_wait(&full[stage], phase, abort_flag, status)) {
                 ok = false;
                 break;
             }
-            for (int gi = 0; gi < Lay::NG; ++gi) {
-                if (!tc_wait(&full[stage], phase, abort_flag, status)) {
-                    ok = false;
-                    break;
-                }
-                tc::fence_after_sync();
+            tc::fence_after_sync();
+            const int nk = (min(TILE_M, g.nx - (t % g.ntx) * TILE_M) + 15) / 16;
+            const uint32_t xs = s0 + stage * Lay::STAGE, ys = xs + Lay::XB;
 #pragma unroll
-                for (int k = 0; k < TILE_M / 16; ++k) {
-                    const uint64_t ad =
-                        tc::smem_desc(a0 + stage * Lay::STAGE + k * 16 * CI * 2, Lay::XB, 8 * CI * 2, Lay::SWX);
-                    const uint64_t bd = tc::smem_desc(y0s + ys * Lay::YB + k * 16 * CO * 2, Lay::YB, 8 * CO * 2, Lay::SWY);
-                    tc::mma_bf16(tbase + (uint32_t)(gi * CO), ad, bd, Lay::IDESC, it > 0 || k > 0);
-                }
-                tc::mma_commit(&empty[stage]);
-                if (++stage == NSTAGE) {
-                    stage = 0;
-                    phase ^= 1u;
+            for (int rg = 0; rg < Lay::NRG; ++rg) {
+#pragma unroll
+                for (int dxi = 0; dxi < 3; ++dxi) {
+                    const uint32_t d = tbase + (uint32_t)((rg * 3 + dxi) * CO);
+                    const uint32_t xa = xs + Lay::group_row0(rg) * Lay::ROW + dxi * 16;
+                    for (int k = 0; k < nk; ++k) {
+                        // 16 voxels per K-step: 16 x 16 bytes into every chunk
+                        const uint64_t ad = tc::smem_desc(xa + k * 256, 128, ROW_CHUNK, tc::SW_NONE);
+                        const uint64_t bd = tc::smem_desc(ys + k * 256, 128, Lay::YCHUNK, tc::SW_NONE);
+                        tc::mma_bf16(d, ad, bd, Lay::IDESC, it > 0 || k > 0);
+                    }
                 }
             }
-            if (ok) tc::mma_commit(&yempty[ys]);
+            tc::mma_commit(&empty[stage]);
+            if (++stage == NSTAGE) {
+                stage = 0;
+                phase ^= 1u;
+            }
         }
         if (ok) tc::mma_commit(accfull);
         tc::mma_commit(drain);
         tc_drain(drain, 0);
     } else if (warp >= 2) {
-        // ---- epilogue: accumulated groups -> this CTA's partial ----
+        // ---- epilogue: bias sums over the staged dY tiles, then the
+        // accumulated groups -> this CTA's partial ----
         const int q = warp & 3;
         const int m = q * 32 + lane;
-        const int tsub = m / CI, ci = m % CI;
+        const int rsub = m / CI, ci = m % CI;
         float* out = partial + (size_t)blockIdx.x * (27 * CO * CI + CO);
         const bool have = t_end > t_begin;
         bool ok = true;
-        if (have) {
-            if (lane == 0) ok = tc_wait(accfull, 0, abort_flag, status);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+        float db[CO];
+#pragma unroll
+        for (int co = 0; co < CO; ++co) db[co] = 0.f;
+        {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int t = t_begin; t < t_end; ++t) {
+                if (!tc_wait_warp(&full[stage], phase, abort_flag, status, lane)) {
+                    ok = false;
+                    break;
+                }
+                if (m < min(TILE_M, g.nx - (t % g.ntx) * TILE_M)) {
+                    const uint4* yt = reinterpret_cast<const uint4*>(sm + stage * Lay::STAGE + Lay::XB);
+#pragma unroll
+                    for (int c = 0; c < CO / 8; ++c) {
+                        const uint4 w = yt[c * (Lay::YCHUNK / 16) + m];
+                        const uint32_t w4[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            db[8 * c + 2 * h] += bf_lo(w4[h]);
+                            db[8 * c + 2 * h + 1] += bf_hi(w4[h]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&empty[stage]);
+                if (++stage == NSTAGE) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+#pragma unroll
+        for (int co = 0; co < CO; ++co) {
+            float v = db[co];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            db[co] = v;
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int co = 0; co < CO; ++co) sbias[q * CO + co] = db[co];
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+        if (q == 0 && lane < CO)
+            out[27 * CO * CI + lane] = ok ? ((sbias[lane] + sbias[CO + lane]) + sbias[2 * CO + lane]) + sbias[3 * CO + lane]
+                                          : 0.f;
+        if (have && ok) {
+            ok = tc_wait_warp(accfull, 0, abort_flag, status, lane);
             if (ok) tc::fence_after_sync();
         }
         if (ok) {
-            for (int gi = 0; gi < Lay::NG; ++gi) {
+            for (int gi = 0; gi < Lay::NGRP; ++gi) {
                 uint32_t r[CO];
                 if (have) {
                     if constexpr (CO == 32)
@@ -510,8 +652,11 @@ __global__ void __launch_bounds__(192) wgrad_tc(const __grid_constant__ CUtensor
 #pragma unroll
                     for (int co = 0; co < CO; ++co) r[co] = 0u;
                 }
-                const int tap = gi * Lay::TG + tsub;
-                if (tap < 27) {
+                const int rg = gi / 3, dxi = gi % 3;
+                const int row = Lay::group_row0(rg) + rsub;
+                const bool owned = rg == 0 || row >= Lay::group_row0(rg - 1) + Lay::TG;
+                if (owned) {
+                    const int tap = row * 3 + dxi;
 #pragma unroll
                     for (int co = 0; co < CO; ++co) out[((size_t)tap * CO + co) * CI + ci] = __uint_as_float(r[co]);
                 }
@@ -523,28 +668,6 @@ __global__ void __launch_bounds__(192) wgrad_tc(const __grid_constant__ CUtensor
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tbase, Lay::TCOLS);
-    }
-}
-
-// Bias gradient db[co] = sum_p dY[p][co], one partial per CTA written beside
-// the weight partial ([27][CO][CI] then [CO]).
-template <int CI, int CO>
-__global__ void __launch_bounds__(256) bias_grad(const __nv_bfloat16* __restrict__ dY, float* __restrict__ partial,
-                                                 long P) {
-    __shared__ float sh[256];
-    const int co = threadIdx.x % CO, grp = threadIdx.x / CO;
-    constexpr int NGRP = 256 / CO;
-    const long chunk = (P + gridDim.x - 1) / gridDim.x;
-    const long p0 = blockIdx.x * chunk, p1 = min(P, p0 + chunk);
-    const unsigned short* d = reinterpret_cast<const unsigned short*>(dY);
-    float a = 0.f;
-    for (long p = p0 + grp; p < p1; p += NGRP) a += __uint_as_float((uint32_t)__ldg(d + p * CO + co) << 16);
-    sh[threadIdx.x] = a;
-    __syncthreads();
-    if (grp == 0) {
-        float s = 0.f;
-        for (int k = 0; k < NGRP; ++k) s += sh[k * CO + co];
-        partial[(size_t)blockIdx.x * (27 * CO * CI + CO) + 27 * CO * CI + co] = s;
     }
 }
 
@@ -628,9 +751,10 @@ __global__ void features(__nv_bfloat16* __restrict__ X0, Shape s, float re_n) {
     f[13] = cospif(zn);
     f[14] = re_n * re_n;
     f[15] = re_n * 0.5f * (yn + 1.f);
-    uint32_t* o = reinterpret_cast<uint32_t*>(X0) + p * 8;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = bf_pack(f[2 * k], f[2 * k + 1]);
+    // channel-chunked: channels 0..7 in chunk plane 0, 8..15 in plane 1
+    uint4* o = reinterpret_cast<uint4*>(X0);
+    o[p] = make_uint4(bf_pack(f[0], f[1]), bf_pack(f[2], f[3]), bf_pack(f[4], f[5]), bf_pack(f[6], f[7]));
+    o[s.P + p] = make_uint4(bf_pack(f[8], f[9]), bf_pack(f[10], f[11]), bf_pack(f[12], f[13]), bf_pack(f[14], f[15]));
 }
 
 // Loss and its gradient: L = mean over voxels and the 4 real channels of
@@ -647,13 +771,14 @@ __global__ void loss_grad(const float* __restrict__ Y, const double* __restrict_
         float d[16] = {0};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const float e = Y[p * 16 + c] - t[c];
+            const float e = Y[p * 4 + c] - t[c];
             l += (double)e * e;
             d[c] = scale * e;
         }
-        uint32_t* o = reinterpret_cast<uint32_t*>(dY) + p * 8;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = bf_pack(d[2 * k], d[2 * k + 1]);
+        // channel-chunked gradient, chunk plane 0 (outputs 0..7); plane 1
+        // (outputs 8..15) stays zero from the network's creation
+        reinterpret_cast<uint4*>(dY)[p] =
+            make_uint4(bf_pack(d[0], d[1]), bf_pack(d[2], d[3]), bf_pack(d[4], d[5]), bf_pack(d[6], d[7]));
     }
     sh[threadIdx.x] = l;
     __syncthreads();
@@ -681,10 +806,10 @@ __global__ void sum_double(const double* __restrict__ partial, long n, double* _
 __global__ void to_fields(const float* __restrict__ Y, double* __restrict__ rho, double* __restrict__ u, Shape s) {
     const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.P) return;
-    rho[p] = 1.0 + (double)Y[p * 16 + 0] / RHO_SCALE;
-    u[p] = (double)Y[p * 16 + 1] / U_SCALE;
-    u[s.P + p] = (double)Y[p * 16 + 2] / U_SCALE;
-    u[2 * s.P + p] = (double)Y[p * 16 + 3] / U_SCALE;
+    rho[p] = 1.0 + (double)Y[p * 4 + 0] / RHO_SCALE;
+    u[p] = (double)Y[p * 4 + 1] / U_SCALE;
+    u[s.P + p] = (double)Y[p * 4 + 2] / U_SCALE;
+    u[2 * s.P + p] = (double)Y[p * 4 + 3] / U_SCALE;
 }
 
 }  // namespace cnn
@@ -706,8 +831,9 @@ struct lbm_cnn {
     float* gpad[cnn::NL];        // padded per-layer gradient (summed partials)
     float* partial;              // weight-gradient partials
     __nv_bfloat16* act[cnn::NL]; // act[0] = input features, act[1..NL-1] hidden activations
-    float* out;                  // [P][16] FP32 prediction
+    float* out;                  // [P][4] FP32 prediction
     __nv_bfloat16* dA[2];        // backward activations (ping-pong)
+    __nv_bfloat16* dY4;          // output-layer gradient, 16 channels chunked (plane 1 always zero)
     double* rho_d;               // FP64 fields (prediction or target staging)
     double* u_d;
     double* lpart;               // loss partials
@@ -716,9 +842,6 @@ struct lbm_cnn {
     int nsm = 0;                 // multiprocessors of the device
     int wg_blocks = 0;           // CTAs of the weight-gradient kernels (one partial each)
     cnn::TileGeom geom;          // 128-voxel tiles of the grid
-    CUtensorMap m_act[cnn::NL];  // act[l] with CH[l] channels
-    CUtensorMap m_dA[2];         // dA[k] with 32 channels
-    CUtensorMap m_dY4;           // dA[1] read as [P][16] (gradient of the output layer)
     CUtensorMap m_wf[cnn::NL];   // forward weights [27][CO][CI]
     CUtensorMap m_wb[cnn::NL];   // backward-data weights [27][CI][CO] (layers 1..NL-1)
     std::string err;
@@ -772,39 +895,16 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Box of one 128-voxel tile: powers of two, x first.
+// Tiles: 128-node segments of the x-rows.
 cnn::TileGeom make_geom(int nx, int ny, int nz) {
-    auto p2 = [](int v) {
-        int r = 1;
-        while (r < v && r < 128) r <<= 1;
-        return r;
-    };
     cnn::TileGeom g;
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.bx = p2(nx);
-    g.by = std::min(128 / g.bx, p2(ny));
-    g.bz = 128 / (g.bx * g.by);
-    g.ntx = (nx + g.bx - 1) / g.bx;
-    g.nty = (ny + g.by - 1) / g.by;
-    g.ntz = (nz + g.bz - 1) / g.bz;
-    g.ntiles = g.ntx * g.nty * g.ntz;
+    g.ntx = (nx + cnn::TILE_M - 1) / cnn::TILE_M;
+    g.ntiles = g.ntx * ny * nz;
+    g.P = (long)nx * ny * nz;
     return g;
-}
-
-// Channel-last activation [nz][ny][nx][C] (BF16) as a 4D tensor map whose box
-// is one tile; 64-byte swizzle for 32 channels, 32-byte for 16.
-bool map_activation(CUtensorMap* m, const void* base, int C, const cnn::TileGeom& g) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)g.nx * C * 2, (cuuint64_t)g.nx * g.ny * C * 2};
-    const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Packed weights [27][CO][CI] (BF16) as one 3D box holding all taps.
@@ -823,35 +923,29 @@ bool map_weights(CUtensorMap* m, const void* base, int CI, int CO) {
 bool make_maps(lbm_cnn* c) {
     bool ok = true;
     for (int l = 0; l < cnn::NL; ++l) {
-        ok = ok && map_activation(&c->m_act[l], c->act[l], cnn::CH[l], c->geom);
         ok = ok && map_weights(&c->m_wf[l], c->wf[l], cnn::CH[l], cnn::CH[l + 1]);
         if (l > 0) ok = ok && map_weights(&c->m_wb[l], c->wb[l], cnn::CH[l + 1], cnn::CH[l]);
     }
-    ok = ok && map_activation(&c->m_dA[0], c->dA[0], 32, c->geom);
-    ok = ok && map_activation(&c->m_dA[1], c->dA[1], 32, c->geom);
-    ok = ok && map_activation(&c->m_dY4, c->dA[1], 16, c->geom);
     return ok;
 }
 
 template <int CI, int CO, int EPI>
-cudaError_t conv(lbm_cnn* c, const CUtensorMap& mapX, const CUtensorMap& mapW, const float* bias, void* Y,
+cudaError_t conv(lbm_cnn* c, const __nv_bfloat16* X, const CUtensorMap& mapW, const float* bias, void* Y,
                  const __nv_bfloat16* gate) {
     const int smem = cnn::ConvLayout<CI, CO, cnn::CONV_STAGES>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(cnn::conv_tc<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int blocks = std::min(c->geom.ntiles, 2 * c->nsm);
-    cnn::conv_tc<CI, CO, EPI><<<blocks, 192, smem, c->stream>>>(mapX, mapW, bias, Y, gate, c->geom, c->status);
+    cnn::conv_tc<CI, CO, EPI><<<blocks, 192, smem, c->stream>>>(X, mapW, bias, Y, gate, c->geom, c->status);
     return cudaGetLastError();
 }
 
 template <int CI, int CO>
-cudaError_t wgrad(lbm_cnn* c, const CUtensorMap& mapX, const CUtensorMap& mapY, const __nv_bfloat16* dY,
-                  float* gpad) {
+cudaError_t wgrad(lbm_cnn* c, const __nv_bfloat16* X, const __nv_bfloat16* dY, float* gpad) {
     const int smem = cnn::WgLayout<CI, CO>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(cnn::wgrad_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    cnn::wgrad_tc<CI, CO><<<c->wg_blocks, 192, smem, c->stream>>>(mapX, mapY, c->partial, c->geom, c->status);
-    cnn::bias_grad<CI, CO><<<c->wg_blocks, 256, 0, c->stream>>>(dY, c->partial, c->s.P);
+    cnn::wgrad_tc<CI, CO><<<c->wg_blocks, 192, smem, c->stream>>>(X, dY, c->partial, c->geom, c->status);
     const int width = 27 * CO * CI + CO;
     cnn::sum_partials<<<(width + 255) / 256, 256, 0, c->stream>>>(c->partial, c->wg_blocks, width, gpad);
     return cudaGetLastError();
@@ -885,27 +979,28 @@ cudaError_t pack_all(lbm_cnn* c) {
 
 cudaError_t forward(lbm_cnn* c) {
     constexpr int L = cnn::NL;
-    cudaError_t e = conv<16, 32, 0>(c, c->m_act[0], c->m_wf[0], c->bias[0], c->act[1], nullptr);
+    cudaError_t e = conv<16, 32, 0>(c, c->act[0], c->m_wf[0], c->bias[0], c->act[1], nullptr);
     for (int l = 1; l < L - 1 && e == cudaSuccess; ++l)
-        e = conv<32, 32, 0>(c, c->m_act[l], c->m_wf[l], c->bias[l], c->act[l + 1], nullptr);
-    if (e == cudaSuccess) e = conv<32, 16, 1>(c, c->m_act[L - 1], c->m_wf[L - 1], c->bias[L - 1], c->out, nullptr);
+        e = conv<32, 32, 0>(c, c->act[l], c->m_wf[l], c->bias[l], c->act[l + 1], nullptr);
+    if (e == cudaSuccess) e = conv<32, 16, 1>(c, c->act[L - 1], c->m_wf[L - 1], c->bias[L - 1], c->out, nullptr);
     return e;
 }
 
-// Backward from dY (held in dA[1] reinterpreted as [P][16]); fills c->grad.
+// Backward from the output-layer gradient dY4 (16 channels, chunked); fills
+// c->grad (weights and biases).
 // The gradient of each hidden activation ping-pongs between dA[0] and dA[1].
 cudaError_t backward(lbm_cnn* c, const __nv_bfloat16* dY4) {
     constexpr int L = cnn::NL;
-    cudaError_t e = wgrad<32, 16>(c, c->m_act[L - 1], c->m_dY4, dY4, c->gpad[L - 1]);
+    cudaError_t e = wgrad<32, 16>(c, c->act[L - 1], dY4, c->gpad[L - 1]);
     // gradient of act[L-1]: conv^T(dY, W_L) masked by act[L-1] > 0
-    if (e == cudaSuccess) e = conv<16, 32, 2>(c, c->m_dY4, c->m_wb[L - 1], nullptr, c->dA[0], c->act[L - 1]);
+    if (e == cudaSuccess) e = conv<16, 32, 2>(c, dY4, c->m_wb[L - 1], nullptr, c->dA[0], c->act[L - 1]);
     int cur = 0;
     for (int l = L - 2; l >= 1 && e == cudaSuccess; --l) {
-        e = wgrad<32, 32>(c, c->m_act[l], c->m_dA[cur], c->dA[cur], c->gpad[l]);
-        if (e == cudaSuccess) e = conv<32, 32, 2>(c, c->m_dA[cur], c->m_wb[l], nullptr, c->dA[cur ^ 1], c->act[l]);
+        e = wgrad<32, 32>(c, c->act[l], c->dA[cur], c->gpad[l]);
+        if (e == cudaSuccess) e = conv<32, 32, 2>(c, c->dA[cur], c->m_wb[l], nullptr, c->dA[cur ^ 1], c->act[l]);
         cur ^= 1;
     }
-    if (e == cudaSuccess) e = wgrad<16, 32>(c, c->m_act[0], c->m_dA[cur], c->dA[cur], c->gpad[0]);
+    if (e == cudaSuccess) e = wgrad<16, 32>(c, c->act[0], c->dA[cur], c->gpad[0]);
     for (int l = 0; l < cnn::NL && e == cudaSuccess; ++l) {
         const int n = 27 * cnn::CH_REAL[l] * cnn::CH_REAL[l + 1];
         cnn::unpack_grad<<<(n + 255) / 256, 256, 0, c->stream>>>(c->gpad[l], c->grad + layer_offset(l),
@@ -996,9 +1091,10 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
         c->act[l] = (__nv_bfloat16*)A(Pn * cnn::CH[l] * 2);
     }
     c->partial = (float*)A((size_t)c->wg_blocks * maxw * 4);
-    c->out = (float*)A(Pn * 16 * 4);
+    c->out = (float*)A(Pn * 4 * 4);
     c->dA[0] = (__nv_bfloat16*)A(Pn * 32 * 2);
     c->dA[1] = (__nv_bfloat16*)A(Pn * 32 * 2);
+    c->dY4 = (__nv_bfloat16*)A(Pn * 16 * 2);
     c->rho_d = (double*)A(Pn * 8);
     c->u_d = (double*)A(3 * Pn * 8);
     c->lpart = (double*)A(((Pn + 255) / 256) * 8);
@@ -1036,6 +1132,7 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 256, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dY4, 0, Pn * 16 * 2, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_m, 0, NP * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v, 0, NP * 4, c->stream);
     for (int l = 0; l < cnn::NL && e == cudaSuccess; ++l)
@@ -1054,8 +1151,8 @@ lbm_status lbm_cnn_create(lbm_cnn** out, int nx, int ny, int nz, const float* in
 void lbm_cnn_destroy(lbm_cnn* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    void* ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->partial, c->out,   c->dA[0],
-                    c->dA[1],  c->rho_d, c->u_d,  c->lpart,  c->lsum,    c->status};
+    void* ptrs[] = {c->master, c->grad, c->adam_m, c->adam_v, c->partial, c->out,  c->dA[0],
+                    c->dA[1],  c->dY4,  c->rho_d, c->u_d,  c->lpart,  c->lsum, c->status};
     for (void* p : ptrs) cnn_free(c, p);
     for (int l = 0; l < cnn::NL; ++l) {
         cnn_free(c, c->wf[l]);
@@ -1101,7 +1198,8 @@ lbm_status lbm_cnn_set_input_raw(lbm_cnn* c, const float* x, size_t count) {
     if (e != cudaSuccess) return cnn_cuda_fail(c, e, "lbm_cnn_set_input_raw");
     std::vector<__nv_bfloat16> hb((size_t)c->s.P * 16);
     for (long p = 0; p < c->s.P; ++p)
-        for (int k = 0; k < 16; ++k) hb[p * 16 + k] = __float2bfloat16_rn(in[p * cnn::C_IN_REAL + k]);
+        for (int k = 0; k < 16; ++k)  // channel-chunked layout [2][P][8]
+            hb[((size_t)(k / 8) * c->s.P + p) * 8 + k % 8] = __float2bfloat16_rn(in[p * cnn::C_IN_REAL + k]);
     e = cudaMemcpyAsync(c->act[0], hb.data(), hb.size() * 2, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? LBM_OK : cnn_cuda_fail(c, e, "lbm_cnn_set_input_raw");
@@ -1113,8 +1211,7 @@ lbm_status lbm_cnn_forward(lbm_cnn* c, float* out, size_t count) {
     if (out && count != (size_t)c->s.P * cnn::C_OUT_REAL) return LBM_ERR_ARG;
     cudaError_t e = forward(c);
     if (e == cudaSuccess && out)
-        e = cudaMemcpy2DAsync(out, 4 * sizeof(float), c->out, 16 * sizeof(float), 4 * sizeof(float), (size_t)c->s.P,
-                              cudaMemcpyDefault, c->stream);
+        e = cudaMemcpyAsync(out, c->out, (size_t)c->s.P * 4 * sizeof(float), cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? check_status(c, "lbm_cnn_forward") : cnn_cuda_fail(c, e, "lbm_cnn_forward");
 }
@@ -1125,9 +1222,8 @@ lbm_status lbm_cnn_gradient(lbm_cnn* c, const double* rho, const double* u, doub
     if (grad_out && count != lbm_cnn_param_count()) return LBM_ERR_ARG;
     cudaError_t e = stage_fields(c, rho, u);
     if (e == cudaSuccess) e = forward(c);
-    __nv_bfloat16* dY4 = c->dA[1];
-    if (e == cudaSuccess) e = loss(c, c->rho_d, c->u_d, dY4);
-    if (e == cudaSuccess) e = backward(c, dY4);
+    if (e == cudaSuccess) e = loss(c, c->rho_d, c->u_d, c->dY4);
+    if (e == cudaSuccess) e = backward(c, c->dY4);
     double l = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, c->lsum, 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && grad_out)

@@ -15,23 +15,14 @@ namespace tc {
 using lbm::smem_u32;
 
 // ---------------------------------------------------------------------------
-// Tensor-map (tiled) TMA loads global -> shared, completion counted on an
-// mbarrier.  c0 is the innermost coordinate (the channel index, always 0 here,
-// so the 16-byte rule on the innermost coordinate holds); the others may be
-// negative or beyond the extent, where the copy writes zeros.
+// Tensor-map (tiled) TMA load global -> shared, completion counted on an
+// mbarrier (the packed weights: c0, the innermost coordinate, is always 0, so
+// the 16-byte rule on the innermost coordinate holds).
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
         "[%5];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
@@ -69,6 +60,11 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 // 8-row groups, the leading offset is unused inside one swizzle atom.
 // MN-major operands (M or N contiguous): the leading offset steps between
 // swizzle atoms along M/N, the stride offset between 8-row groups along K.
+// Unswizzled (core matrices of 8 rows x 16 bytes stored as 128 contiguous
+// bytes): K-major, the leading offset steps between core matrices along K
+// and the stride offset between 8-row groups along M; MN-major, the leading
+// offset steps between 8-row groups along K and the stride offset between
+// core matrices along M/N.
 enum : uint32_t { SW_NONE = 0, SW_32B = 6, SW_64B = 4, SW_128B = 2 };
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes, uint32_t swz) {
