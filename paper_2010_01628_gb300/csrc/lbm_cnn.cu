@@ -190,12 +190,10 @@ __device__ __forceinline__ void zero_row_cells(uint8_t* slot, const RowRun& r, i
     }
 }
 
-// Lane 0: the bulk copies of a staged row's in-grid run, one per chunk.
-template <int NCH>
-__device__ __forceinline__ void copy_row(uint8_t* slot, const __nv_bfloat16* X, long P, const RowRun& r,
-                                         uint64_t* bar) {
-    if (r.n == 0) return;
-    for (int c = 0; c < NCH; ++c)
+// The bulk copy of chunk c of a staged row's in-grid run.
+__device__ __forceinline__ void copy_row_chunk(uint8_t* slot, const __nv_bfloat16* X, long P, const RowRun& r, int c,
+                                               uint64_t* bar) {
+    if (r.n > 0)
         lbm::bulk_g2s(slot + c * ROW_CHUNK + r.c0 * 16, X + ((size_t)c * P + r.src) * 8, (uint32_t)r.n * 16u, bar);
 }
 
@@ -208,6 +206,7 @@ struct ConvLayout {
     static constexpr int BAR_OFF = (A_OFF + NSTAGE * A_STRIDE + 7) / 8 * 8;
     static constexpr int NBAR = 2 * NSTAGE + 6;  // full, empty, tmem full x2, tmem empty x2, weights, drain
     static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 1024;  // + TMEM slot, abort flag, alignment slack
+    static constexpr uint32_t TCOLS = 2 * CO <= 32 ? 32 : 64;       // two accumulators of CO columns
     static constexpr uint32_t SWZ_W = CI == 32 ? tc::SW_64B : tc::SW_32B;
     static constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_M, CO, false, false);
     static_assert(A_OFF % 1024 == 0 && A_STRIDE % 128 == 0, "weights on the swizzle period, slots 128-byte aligned");
@@ -216,11 +215,10 @@ struct ConvLayout {
 constexpr int CONV_STAGES = 6;
 
 // EPI: 0 = +bias, ReLU, BF16 out (chunked); 1 = +bias, FP32 out [P][4] (the
-// output layer's real channels);
-// 2 = zero where `gate` (this layer's forward activation, chunked) is not
-// positive, BF16 out (chunked), no bias.
+// output layer's real channels); 2 = zero where `gate` (this layer's forward
+// activation, chunked) is not positive, BF16 out (chunked), no bias.
 template <int CI, int CO, int EPI>
-__global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__ X,
+__global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restrict__ X,
                                                const __grid_constant__ CUtensorMap mapW, const float* __restrict__ bias,
                                                void* __restrict__ Y, const __nv_bfloat16* __restrict__ gate,
                                                TileGeom g, int* status) {
@@ -239,6 +237,14 @@ __global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__
     uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Rows of one tile: the copies always fill cells 1 .. nx, so the halo
+    // cells stay as zeroed here; only rows outside the grid are written over.
+    const bool fixed_halo = g.ntx == 1;
+    if (fixed_halo) {
+        for (int i = threadIdx.x; i < NSTAGE * Lay::A_STRIDE / 16; i += blockDim.x)
+            reinterpret_cast<uint4*>(sA)[i] = make_uint4(0u, 0u, 0u, 0u);
+        lbm::fence_proxy_async();
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__
         lbm::fence_barrier_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(tslot, 64);
+        tc::tmem_alloc(tslot, Lay::TCOLS);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -285,14 +291,18 @@ __global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__
                 }
                 const RowRun run = row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1);
                 uint8_t* slot = sA + stage * Lay::A_STRIDE;
-                zero_row_cells<CI / 8>(slot, run, lane);
-                lbm::fence_proxy_async();
-                __syncwarp();
+                if (!fixed_halo || run.n == 0) {
+                    zero_row_cells<CI / 8>(slot, run, lane);
+                    lbm::fence_proxy_async();
+                    __syncwarp();
+                }
+                // lane 0 arms the stage, lanes 0 .. CI/8 - 1 issue one chunk each
                 if (lane == 0) {
                     lbm::mbar_arrive_expect_tx(&full[stage], (uint32_t)((CI / 8) * run.n * 16));
-                    copy_row<CI / 8>(slot, X, g.P, run, &full[stage]);
                     armed[stage] = (int)phase;
                 }
+                __syncwarp();
+                if (lane < CI / 8) copy_row_chunk(slot, X, g.P, run, lane, &full[stage]);
                 if (++stage == NSTAGE) {
                     stage = 0;
                     phase ^= 1u;
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__
             tc_drain(wfull, 0);
         }
     } else if (threadIdx.x == 32) {
-        // ---- MMA issuer: three taps (dx = -1, 0, 1) per staged row ----
+        // ---- MMA issuer: the three taps (dx = -1, 0, 1) of each staged row ----
         if (tc_wait(wfull, 0, abort_flag, status)) {
             tc::fence_after_sync();
             int stage = 0;
@@ -359,25 +369,25 @@ __global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__
         int it = 0;
         for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x, ++it) {
             const int acc = it & 1;
+            const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CO);
             if (!tc_wait_warp(&tfull[acc], ((uint32_t)it >> 1) & 1u, abort_flag, status, lane)) break;
             tc::fence_after_sync();
             uint32_t r[CO];
-            if constexpr (CO == 32)
-                tc::tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CO), r);
-            else
-                tc::tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * CO), r);
+            if constexpr (CO == 32) tc::tmem_ld32(tl, r); else tc::tmem_ld16(tl, r);
             tc::tmem_ld_wait();
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+            float v[CO];
+#pragma unroll
+            for (int co = 0; co < CO; ++co) v[co] = __uint_as_float(r[co]);
             int x0, y0, z0;
             tile_origin(g, t, x0, y0, z0);
             const int x = x0 + row;
             if (x >= g.nx) continue;
             const long p = ((long)z0 * g.ny + y0) * g.nx + x;
-            float v[CO];
 #pragma unroll
-            for (int co = 0; co < CO; ++co) v[co] = __uint_as_float(r[co]) + bvals[co];
+            for (int co = 0; co < CO; ++co) v[co] += bvals[co];
             if (EPI == 0) {
 #pragma unroll
                 for (int co = 0; co < CO; ++co) v[co] = fmaxf(v[co], 0.f);
@@ -409,7 +419,7 @@ __global__ void __launch_bounds__(192) conv_tc(const __nv_bfloat16* __restrict__
     __syncthreads();
     if (warp == 1) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tbase, 64);
+        tc::tmem_dealloc(tbase, Lay::TCOLS);
     }
 }
 
@@ -526,14 +536,21 @@ __global__ void __launch_bounds__(192) wgrad_tc(const __nv_bfloat16* __restrict_
             __syncwarp();
             if (lane == 0) {
                 lbm::mbar_arrive_expect_tx(&full[stage], bytes + (uint32_t)((CO / 8) * nv * 16));
-                for (int r = 0; r < 9; ++r)
-                    copy_row<CI / 8>(sx + r * Lay::ROW, X, g.P, row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1),
-                                     &full[stage]);
-                const long p0 = ((long)z0 * g.ny + y0) * g.nx + x0;
-                for (int c = 0; c < CO / 8; ++c)
+                armed[stage] = (int)phase;
+            }
+            __syncwarp();
+            // the 9 x CI/8 row-chunk copies and the CO/8 dY copies, spread over the lanes
+            for (int i = lane; i < 9 * (CI / 8) + CO / 8; i += 32) {
+                if (i < 9 * (CI / 8)) {
+                    const int r = i / (CI / 8), c = i % (CI / 8);
+                    copy_row_chunk(sx + r * Lay::ROW, X, g.P, row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1), c,
+                                   &full[stage]);
+                } else {
+                    const int c = i - 9 * (CI / 8);
+                    const long p0 = ((long)z0 * g.ny + y0) * g.nx + x0;
                     lbm::bulk_g2s(sy + c * Lay::YCHUNK, dY + ((size_t)c * g.P + p0) * 8, (uint32_t)nv * 16u,
                                   &full[stage]);
-                armed[stage] = (int)phase;
+                }
             }
             if (++stage == NSTAGE) {
                 stage = 0;
