@@ -197,22 +197,28 @@ __device__ __forceinline__ void copy_row_chunk(uint8_t* slot, const __nv_bfloat1
         lbm::bulk_g2s(slot + c * ROW_CHUNK + r.c0 * 16, X + ((size_t)c * P + r.src) * 8, (uint32_t)r.n * 16u, bar);
 }
 
-template <int CI, int CO, int NSTAGE>
+// A ring stage holds RPS staged rows (RPS = 3: the rows dy = -1, 0, 1 of one
+// dz), handed from the producer to the MMAs by one barrier.
+template <int CI, int CO, int NSTAGE, int RPS>
 struct ConvLayout {
     static constexpr int A_BYTES = (CI / 8) * ROW_CHUNK;          // a staged row, all chunks
-    static constexpr int A_STRIDE = (A_BYTES + 127) / 128 * 128;  // ring slots on 128-byte boundaries
+    static constexpr int A_STRIDE = (A_BYTES + 127) / 128 * 128;  // row slots on 128-byte boundaries
+    static constexpr int STAGE_BYTES = RPS * A_STRIDE;
     static constexpr int W_BYTES = 27 * CO * CI * 2;
     static constexpr int A_OFF = (W_BYTES + 1023) / 1024 * 1024;
-    static constexpr int BAR_OFF = (A_OFF + NSTAGE * A_STRIDE + 7) / 8 * 8;
+    static constexpr int BAR_OFF = (A_OFF + NSTAGE * STAGE_BYTES + 7) / 8 * 8;
     static constexpr int NBAR = 2 * NSTAGE + 6;  // full, empty, tmem full x2, tmem empty x2, weights, drain
     static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16 + 1024;  // + TMEM slot, abort flag, alignment slack
     static constexpr uint32_t TCOLS = 2 * CO <= 32 ? 32 : 64;       // two accumulators of CO columns
     static constexpr uint32_t SWZ_W = CI == 32 ? tc::SW_64B : tc::SW_32B;
     static constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_M, CO, false, false);
     static_assert(A_OFF % 1024 == 0 && A_STRIDE % 128 == 0, "weights on the swizzle period, slots 128-byte aligned");
+    static_assert(9 % RPS == 0, "a tile's nine rows fill whole stages");
+    static_assert(RPS * (CI / 8) <= 32, "one producer lane per row chunk of a stage");
 };
 
-constexpr int CONV_STAGES = 6;
+constexpr int CONV_STAGES = 2;
+constexpr int CONV_RPS = 3;
 
 // EPI: 0 = +bias, ReLU, BF16 out (chunked); 1 = +bias, FP32 out [P][4] (the
 // output layer's real channels); 2 = zero where `gate` (this layer's forward
@@ -222,7 +228,8 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
                                                const __grid_constant__ CUtensorMap mapW, const float* __restrict__ bias,
                                                void* __restrict__ Y, const __nv_bfloat16* __restrict__ gate,
                                                TileGeom g, int* status) {
-    using Lay = ConvLayout<CI, CO, CONV_STAGES>;
+    using Lay = ConvLayout<CI, CO, CONV_STAGES, CONV_RPS>;
+    constexpr int RPS = CONV_RPS;
     constexpr int NSTAGE = CONV_STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = align1024(smem_raw);
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
     // cells stay as zeroed here; only rows outside the grid are written over.
     const bool fixed_halo = g.ntx == 1;
     if (fixed_halo) {
-        for (int i = threadIdx.x; i < NSTAGE * Lay::A_STRIDE / 16; i += blockDim.x)
+        for (int i = threadIdx.x; i < NSTAGE * Lay::STAGE_BYTES / 16; i += blockDim.x)
             reinterpret_cast<uint4*>(sA)[i] = make_uint4(0u, 0u, 0u, 0u);
         lbm::fence_proxy_async();
     }
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
-        // ---- producer warp: 9 staged rows per tile ----
+        // ---- producer warp: 9 staged rows per tile, RPS per stage ----
         if (lane == 0) {
             tc::prefetch_map(&mapW);
             lbm::mbar_arrive_expect_tx(wfull, Lay::W_BYTES);
@@ -284,25 +291,37 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
         for (int t = blockIdx.x; t < g.ntiles && ok; t += gridDim.x) {
             int x0, y0, z0;
             tile_origin(g, t, x0, y0, z0);
-            for (int r = 0; r < 9; ++r) {
+            for (int r0 = 0; r0 < 9; r0 += RPS) {
                 if (!tc_wait_warp(&empty[stage], phase ^ 1u, abort_flag, status, lane)) {
                     ok = false;
                     break;
                 }
-                const RowRun run = row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1);
-                uint8_t* slot = sA + stage * Lay::A_STRIDE;
-                if (!fixed_halo || run.n == 0) {
-                    zero_row_cells<CI / 8>(slot, run, lane);
-                    lbm::fence_proxy_async();
-                    __syncwarp();
+                uint8_t* st = sA + stage * Lay::STAGE_BYTES;
+                uint32_t bytes = 0;
+                bool zeroed = false;
+#pragma unroll
+                for (int j = 0; j < RPS; ++j) {
+                    const int r = r0 + j;
+                    const RowRun run = row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1);
+                    if (!fixed_halo || run.n == 0) {
+                        zero_row_cells<CI / 8>(st + j * Lay::A_STRIDE, run, lane);
+                        zeroed = true;
+                    }
+                    bytes += (uint32_t)((CI / 8) * run.n * 16);
                 }
-                // lane 0 arms the stage, lanes 0 .. CI/8 - 1 issue one chunk each
+                if (zeroed) lbm::fence_proxy_async();
+                __syncwarp();
+                // lane 0 arms the stage, the lanes issue one row chunk each
                 if (lane == 0) {
-                    lbm::mbar_arrive_expect_tx(&full[stage], (uint32_t)((CI / 8) * run.n * 16));
+                    lbm::mbar_arrive_expect_tx(&full[stage], bytes);
                     armed[stage] = (int)phase;
                 }
                 __syncwarp();
-                if (lane < CI / 8) copy_row_chunk(slot, X, g.P, run, lane, &full[stage]);
+                if (lane < RPS * (CI / 8)) {
+                    const int j = lane / (CI / 8), r = r0 + j;
+                    copy_row_chunk(st + j * Lay::A_STRIDE, X, g.P, row_run(g, x0, y0 + r % 3 - 1, z0 + r / 3 - 1),
+                                   lane % (CI / 8), &full[stage]);
+                }
                 if (++stage == NSTAGE) {
                     stage = 0;
                     phase ^= 1u;
@@ -329,23 +348,27 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
                 if (!tc_wait(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, abort_flag, status)) break;
                 tc::fence_after_sync();
                 const uint32_t d = tbase + (uint32_t)(acc * CO);
-                for (int r = 0; r < 9; ++r) {
+                for (int r0 = 0; r0 < 9; r0 += RPS) {
                     if (!tc_wait(&full[stage], phase, abort_flag, status)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t arow = a0 + stage * Lay::A_STRIDE;
 #pragma unroll
-                    for (int dxi = 0; dxi < 3; ++dxi) {
-                        const int tap = r * 3 + dxi;  // (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+                    for (int j = 0; j < RPS; ++j) {
+                        const int r = r0 + j;
+                        const uint32_t arow = a0 + stage * Lay::STAGE_BYTES + j * Lay::A_STRIDE;
 #pragma unroll
-                        for (int k = 0; k < CI / 16; ++k) {
-                            const uint64_t ad =
-                                tc::smem_desc(arow + dxi * 16 + k * 2 * ROW_CHUNK, ROW_CHUNK, 128, tc::SW_NONE);
-                            const uint64_t bd =
-                                tc::smem_desc(w0 + tap * CO * CI * 2 + k * 32, 16, 8 * CI * 2, Lay::SWZ_W);
-                            tc::mma_bf16(d, ad, bd, Lay::IDESC, r > 0 || dxi > 0 || k > 0);
+                        for (int dxi = 0; dxi < 3; ++dxi) {
+                            const int tap = r * 3 + dxi;  // (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+#pragma unroll
+                            for (int k = 0; k < CI / 16; ++k) {
+                                const uint64_t ad =
+                                    tc::smem_desc(arow + dxi * 16 + k * 2 * ROW_CHUNK, ROW_CHUNK, 128, tc::SW_NONE);
+                                const uint64_t bd =
+                                    tc::smem_desc(w0 + tap * CO * CI * 2 + k * 32, 16, 8 * CI * 2, Lay::SWZ_W);
+                                tc::mma_bf16(d, ad, bd, Lay::IDESC, r > 0 || dxi > 0 || k > 0);
+                            }
                         }
                     }
                     tc::mma_commit(&empty[stage]);
@@ -949,7 +972,7 @@ bool make_maps(lbm_cnn* c) {
 template <int CI, int CO, int EPI>
 cudaError_t conv(lbm_cnn* c, const __nv_bfloat16* X, const CUtensorMap& mapW, const float* bias, void* Y,
                  const __nv_bfloat16* gate) {
-    const int smem = cnn::ConvLayout<CI, CO, cnn::CONV_STAGES>::BYTES;
+    const int smem = cnn::ConvLayout<CI, CO, cnn::CONV_STAGES, cnn::CONV_RPS>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(cnn::conv_tc<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int blocks = std::min(c->geom.ntiles, 2 * c->nsm);
