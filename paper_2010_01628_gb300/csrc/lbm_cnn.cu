@@ -342,7 +342,9 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
             uint32_t phase = 0;
             int it = 0;
             bool ok = true;
-            const uint32_t a0 = lbm::smem_u32(sA), w0 = lbm::smem_u32(sW);
+            // descriptors built once, advanced by byte offsets per operand
+            const uint64_t adesc0 = tc::smem_desc(lbm::smem_u32(sA), ROW_CHUNK, 128, tc::SW_NONE);
+            const uint64_t wdesc0 = tc::smem_desc(lbm::smem_u32(sW), 16, 8 * CI * 2, Lay::SWZ_W);
             for (int t = blockIdx.x; t < g.ntiles && ok; t += gridDim.x, ++it) {
                 const int acc = it & 1;
                 if (!tc_wait(&tempty[acc], (((uint32_t)it >> 1) & 1u) ^ 1u, abort_flag, status)) break;
@@ -354,20 +356,19 @@ __global__ void __launch_bounds__(192, 2) conv_tc(const __nv_bfloat16* __restric
                         break;
                     }
                     tc::fence_after_sync();
+                    const uint64_t astage = tc::desc_advance(adesc0, stage * Lay::STAGE_BYTES);
+                    const uint64_t wstage = tc::desc_advance(wdesc0, r0 * 3 * CO * CI * 2);  // tap 3 r0 onwards
 #pragma unroll
                     for (int j = 0; j < RPS; ++j) {
-                        const int r = r0 + j;
-                        const uint32_t arow = a0 + stage * Lay::STAGE_BYTES + j * Lay::A_STRIDE;
 #pragma unroll
                         for (int dxi = 0; dxi < 3; ++dxi) {
-                            const int tap = r * 3 + dxi;  // (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+                            // tap (r0 + j) * 3 + dxi = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
 #pragma unroll
                             for (int k = 0; k < CI / 16; ++k) {
                                 const uint64_t ad =
-                                    tc::smem_desc(arow + dxi * 16 + k * 2 * ROW_CHUNK, ROW_CHUNK, 128, tc::SW_NONE);
-                                const uint64_t bd =
-                                    tc::smem_desc(w0 + tap * CO * CI * 2 + k * 32, 16, 8 * CI * 2, Lay::SWZ_W);
-                                tc::mma_bf16(d, ad, bd, Lay::IDESC, r > 0 || dxi > 0 || k > 0);
+                                    tc::desc_advance(astage, j * Lay::A_STRIDE + dxi * 16 + k * 2 * ROW_CHUNK);
+                                const uint64_t bd = tc::desc_advance(wstage, (j * 3 + dxi) * CO * CI * 2 + k * 32);
+                                tc::mma_bf16(d, ad, bd, Lay::IDESC, r0 > 0 || j > 0 || dxi > 0 || k > 0);
                             }
                         }
                     }
@@ -585,7 +586,8 @@ __global__ void __launch_bounds__(192) wgrad_tc(const __nv_bfloat16* __restrict_
                 if (armed[s] >= 0) tc_drain(&full[s], (uint32_t)armed[s]);
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer ----
-        const uint32_t s0 = lbm::smem_u32(sm);
+        const uint64_t xdesc0 = tc::smem_desc(lbm::smem_u32(sm), 128, ROW_CHUNK, tc::SW_NONE);
+        const uint64_t ydesc0 = tc::smem_desc(lbm::smem_u32(sm) + Lay::XB, 128, Lay::YCHUNK, tc::SW_NONE);
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -596,20 +598,26 @@ __global__ void __launch_bounds__(192) wgrad_tc(const __nv_bfloat16* __restrict_
             }
             tc::fence_after_sync();
             const int nk = (min(TILE_M, g.nx - (t % g.ntx) * TILE_M) + 15) / 16;
-            const uint32_t xs = s0 + stage * Lay::STAGE, ys = xs + Lay::XB;
+            const uint64_t xst = tc::desc_advance(xdesc0, stage * Lay::STAGE);
+            const uint64_t yst = tc::desc_advance(ydesc0, stage * Lay::STAGE);
+            // 16 voxels per K-step: 16 x 16 bytes into every chunk
+            if (nk == TILE_M / 16) {
 #pragma unroll
-            for (int rg = 0; rg < Lay::NRG; ++rg) {
+                for (int rg = 0; rg < Lay::NRG; ++rg)
 #pragma unroll
-                for (int dxi = 0; dxi < 3; ++dxi) {
-                    const uint32_t d = tbase + (uint32_t)((rg * 3 + dxi) * CO);
-                    const uint32_t xa = xs + Lay::group_row0(rg) * Lay::ROW + dxi * 16;
-                    for (int k = 0; k < nk; ++k) {
-                        // 16 voxels per K-step: 16 x 16 bytes into every chunk
-                        const uint64_t ad = tc::smem_desc(xa + k * 256, 128, ROW_CHUNK, tc::SW_NONE);
-                        const uint64_t bd = tc::smem_desc(ys + k * 256, 128, Lay::YCHUNK, tc::SW_NONE);
-                        tc::mma_bf16(d, ad, bd, Lay::IDESC, it > 0 || k > 0);
-                    }
-                }
+                    for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                        for (int k = 0; k < TILE_M / 16; ++k)
+                            tc::mma_bf16(tbase + (uint32_t)((rg * 3 + dxi) * CO),
+                                         tc::desc_advance(xst, Lay::group_row0(rg) * Lay::ROW + dxi * 16 + k * 256),
+                                         tc::desc_advance(yst, k * 256), Lay::IDESC, it > 0 || k > 0);
+            } else {
+                for (int rg = 0; rg < Lay::NRG; ++rg)
+                    for (int dxi = 0; dxi < 3; ++dxi)
+                        for (int k = 0; k < nk; ++k)
+                            tc::mma_bf16(tbase + (uint32_t)((rg * 3 + dxi) * CO),
+                                         tc::desc_advance(xst, Lay::group_row0(rg) * Lay::ROW + dxi * 16 + k * 256),
+                                         tc::desc_advance(yst, k * 256), Lay::IDESC, it > 0 || k > 0);
             }
             tc::mma_commit(&empty[stage]);
             if (++stage == NSTAGE) {

@@ -77,6 +77,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
     return d;
 }
 
+// The descriptor of the same matrix `bytes` further on (16-byte multiple): the
+// start-address field holds address >> 4 in its low 14 bits, and shared
+// addresses stay below 2^18, so the add never carries out of it.
+__device__ __forceinline__ uint64_t desc_advance(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
 // Instruction descriptor of kind::f16 (32 bits): D FP32 (bits 4-5 = 1), A and
 // B BF16 (bits 7-9 = 1, 10-12 = 1), A/B major (bit 15/16: 0 K-major,
 // 1 MN-major), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
