@@ -806,35 +806,36 @@ __global__ void features(__nv_bfloat16* __restrict__ X0, Shape s, float re_n) {
 }
 
 // Loss and its gradient: L = mean over voxels and the 4 real channels of
-// (Y - T)^2 with T = [(rho - 1) RHO_SCALE, u U_SCALE] from FP64 fields.
-__global__ void loss_grad(const float* __restrict__ Y, const double* __restrict__ rho, const double* __restrict__ u,
-                          __nv_bfloat16* __restrict__ dY, double* __restrict__ partial, Shape s) {
-    __shared__ double sh[256];
-    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    double l = 0.0;
-    if (p < s.P) {
-        const float t[4] = {(float)((rho[p] - 1.0) * RHO_SCALE), (float)(u[p] * U_SCALE), (float)(u[s.P + p] * U_SCALE),
-                            (float)(u[2 * s.P + p] * U_SCALE)};
-        const float scale = 2.f / (4.f * (float)s.P);
-        float d[16] = {0};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float e = Y[p * 4 + c] - t[c];
-            l += (double)e * e;
-            d[c] = scale * e;
-        }
+// (Y - T)^2 with T = [(rho - 1) RHO_SCALE, u U_SCALE] from FP64 fields
+// (rho - 1 taken in FP64).  Grid-stride; each thread sums its squared errors
+// in FP32, the block's in FP64 (one partial per block).
+__global__ void __launch_bounds__(256) loss_grad(const float* __restrict__ Y, const double* __restrict__ rho,
+                                                 const double* __restrict__ u, __nv_bfloat16* __restrict__ dY,
+                                                 double* __restrict__ partial, Shape s) {
+    __shared__ double sh[8];
+    const float scale = 2.f / (4.f * (float)s.P);
+    float l = 0.f;
+    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < s.P; p += (long)gridDim.x * blockDim.x) {
+        const float4 y = reinterpret_cast<const float4*>(Y)[p];
+        const float e0 = y.x - (float)((__ldg(rho + p) - 1.0) * RHO_SCALE);
+        const float e1 = y.y - (float)(__ldg(u + p) * U_SCALE);
+        const float e2 = y.z - (float)(__ldg(u + s.P + p) * U_SCALE);
+        const float e3 = y.w - (float)(__ldg(u + 2 * s.P + p) * U_SCALE);
+        l += (e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3);
         // channel-chunked gradient, chunk plane 0 (outputs 0..7); plane 1
         // (outputs 8..15) stays zero from the network's creation
         reinterpret_cast<uint4*>(dY)[p] =
-            make_uint4(bf_pack(d[0], d[1]), bf_pack(d[2], d[3]), bf_pack(d[4], d[5]), bf_pack(d[6], d[7]));
+            make_uint4(bf_pack(scale * e0, scale * e1), bf_pack(scale * e2, scale * e3), 0u, 0u);
     }
-    sh[threadIdx.x] = l;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)l;
     __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-        if ((int)threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        partial[blockIdx.x] = t;
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
 __global__ void sum_double(const double* __restrict__ partial, long n, double* __restrict__ out) {
@@ -1062,7 +1063,7 @@ cudaError_t backward(lbm_cnn* c, const __nv_bfloat16* dY4) {
 // Loss against FP64 target fields (device, planar rho [P], u [3P]); writes
 // dY4 into its buffer and the loss sum into c->lsum.
 cudaError_t loss(lbm_cnn* c, const double* rho, const double* u, __nv_bfloat16* dY4) {
-    const long blocks = (c->s.P + 255) / 256;
+    const long blocks = std::min<long>((c->s.P + 255) / 256, 4L * c->nsm);
     cnn::loss_grad<<<(unsigned)blocks, 256, 0, c->stream>>>(c->out, rho, u, dY4, c->lpart, c->s);
     cnn::sum_double<<<1, 256, 0, c->stream>>>(c->lpart, blocks, c->lsum);
     return cudaGetLastError();
@@ -1075,11 +1076,30 @@ lbm_status cnn_cuda_fail(lbm_cnn* c, cudaError_t e, const char* where) {
     return LBM_ERR_CUDA;
 }
 
-// Stage FP64 target fields (host or device pointers) into the CNN's buffers.
-cudaError_t stage_fields(lbm_cnn* c, const double* rho, const double* u) {
+bool device_accessible(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
+// FP64 target fields for the loss: device pointers of this device are read in
+// place; host pointers are staged into the network's buffers.
+cudaError_t stage_fields(lbm_cnn* c, const double*& rho, const double*& u) {
     const size_t P = (size_t)c->s.P;
-    cudaError_t e = cudaMemcpyAsync(c->rho_d, rho, P * 8, cudaMemcpyDefault, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->u_d, u, 3 * P * 8, cudaMemcpyDefault, c->stream);
+    cudaError_t e = cudaSuccess;
+    if (!device_accessible(rho)) {
+        e = cudaMemcpyAsync(c->rho_d, rho, P * 8, cudaMemcpyDefault, c->stream);
+        rho = c->rho_d;
+    }
+    if (e == cudaSuccess && !device_accessible(u)) {
+        e = cudaMemcpyAsync(c->u_d, u, 3 * P * 8, cudaMemcpyDefault, c->stream);
+        u = c->u_d;
+    }
     return e;
 }
 
@@ -1270,7 +1290,7 @@ lbm_status lbm_cnn_gradient(lbm_cnn* c, const double* rho, const double* u, doub
     if (grad_out && count != lbm_cnn_param_count()) return LBM_ERR_ARG;
     cudaError_t e = stage_fields(c, rho, u);
     if (e == cudaSuccess) e = forward(c);
-    if (e == cudaSuccess) e = loss(c, c->rho_d, c->u_d, c->dY4);
+    if (e == cudaSuccess) e = loss(c, rho, u, c->dY4);
     if (e == cudaSuccess) e = backward(c, c->dY4);
     double l = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&l, c->lsum, 8, cudaMemcpyDeviceToHost, c->stream);
