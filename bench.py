@@ -710,6 +710,11 @@ def run_ours(args):
         u_o = torch.empty_like(u_h).pin_memory()
         c3 = L.lbm_create((n, n, n), 1 / TAU, g=G, precision=prec)
         apply_launch(L, c3, args.launch, tune_cache)
+        # one untimed pass through the same calls (first-use costs of the copy path)
+        L.lbm_init_fields(c3, rho_h, u_h)
+        L.lbm_step(c3, 1)
+        L.lbm_fields(c3, (n, n, n), rho=rho_o, u=u_o)
+        torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         L.lbm_init_fields(c3, rho_h, u_h)

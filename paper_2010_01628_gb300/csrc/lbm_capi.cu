@@ -117,7 +117,27 @@ void release_all(lbm_ctx* c) {
     dev_free(c, c->staging);
     dev_free(c, c->status);
     if (c->result_host) cudaFreeHost(c->result_host);
+    for (int b = 0; b < 2; ++b) {
+        if (c->slab_ready[b]) cudaEventDestroy(c->slab_ready[b]);
+        if (c->slab_free[b]) cudaEventDestroy(c->slab_free[b]);
+    }
+    if (c->fields_start) cudaEventDestroy(c->fields_start);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
+
+// The copy stream and the events of the double-buffered field slabs.
+bool make_copy_stream(lbm_ctx* c) {
+    bool ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaEventCreateWithFlags(&c->slab_ready[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->slab_free[b], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->fields_start, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    return ok;
+}
+
+// Field slab b of the two (8 FP64 planes of staging_cells each).
+double* slab_buf(lbm_ctx* c, int b) { return c->staging + (size_t)b * 8 * c->staging_cells; }
 
 // Status word of the bounded device waits (TMA-staged kernel); read after a
 // synchronisation.
@@ -166,8 +186,9 @@ lbm_status lbm_internal_alloc_batch(lbm_ctx* c, size_t state_elems, size_t cells
     c->uprev = dev_alloc(c, 3 * cells * cb);
     c->partials = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH * lbm::RED_BLOCKS);
     c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
-    c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
+    c->staging = (double*)dev_alloc(c, sizeof(double) * 2 * 8 * c->staging_cells);
     if (!(c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging)) return LBM_ERR_OOM;
+    if (!make_copy_stream(c)) return LBM_ERR_CUDA;
     // colour gradient: phi and rho_r of every domain's nodes; Shan-Chen: psi;
     // rebuilt each step
     if (c->physics == LBM_PHYS_CGM || c->physics == LBM_PHYS_SC) {
@@ -295,13 +316,13 @@ lbm_status lbm_create(lbm_ctx** out, const lbm_grid* grid, lbm_lattice lattice, 
     c->uprev = dev_alloc(c, 3 * c->box.n * cb);
     c->partials = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH * lbm::RED_BLOCKS);
     c->result = (double*)dev_alloc(c, sizeof(double) * lbm::RED_WIDTH);
-    c->staging = (double*)dev_alloc(c, sizeof(double) * 8 * c->staging_cells);
+    c->staging = (double*)dev_alloc(c, sizeof(double) * 2 * 8 * c->staging_cells);
     const bool has_phi = physics == LBM_PHYS_CGM || physics == LBM_PHYS_SC;
     // scratch: psi (Shan-Chen); phi and the red density (colour gradient)
     if (has_phi) c->phi = dev_alloc(c, (physics == LBM_PHYS_CGM ? 2 : 1) * c->box.n * cb);
     c->status = (int*)dev_alloc(c, 256);
     bool ok = c->buf[0] && c->buf[1] && c->uprev && c->partials && c->result && c->staging && c->status &&
-              (!has_phi || c->phi);
+              (!has_phi || c->phi) && make_copy_stream(c);
     if (ok && cudaMallocHost((void**)&c->result_host, sizeof(double) * lbm::RED_WIDTH) != cudaSuccess) {
         cudaGetLastError();
         c->result_host = nullptr;
@@ -353,30 +374,44 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* u, const
     if (c->physics == LBM_PHYS_CGM && !phase) return fail(c, LBM_ERR_ARG, "CGM needs the phase field%s");
     const size_t n = c->box.n, plane = (size_t)c->box.nx * c->box.ny;
     const int nzs = slab_planes(c);
-    for (int z0 = 0; z0 < c->box.nz; z0 += nzs) {
+    // Two slabs in turn: the copies of slab j (copy stream) overlap the
+    // initialisation kernel of slab j - 1 (the context's stream).
+    cudaStream_t cs = c->copy_stream;
+    cudaError_t e = cudaEventRecord(c->fields_start, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c->fields_start, 0);
+    for (int z0 = 0, j = 0; z0 < c->box.nz && e == cudaSuccess; z0 += nzs, ++j) {
         const int k = (z0 + nzs <= c->box.nz) ? nzs : c->box.nz - z0;
         const size_t m = plane * k, off = plane * z0;
-        double* s = c->staging;
-        cudaError_t e = cudaMemcpyAsync(s, rho + off, m * 8, cudaMemcpyDefault, c->stream);
+        const int b = j & 1;
+        double* s = slab_buf(c, b);
+        if (j >= 2) e = cudaStreamWaitEvent(cs, c->slab_free[b], 0);  // slab j - 2's kernel has read it
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s, rho + off, m * 8, cudaMemcpyDefault, cs);
         for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
             if (u)
-                e = cudaMemcpyAsync(s + (1 + a) * m, u + a * n + off, m * 8, cudaMemcpyDefault, c->stream);
+                e = cudaMemcpyAsync(s + (1 + a) * m, u + a * n + off, m * 8, cudaMemcpyDefault, cs);
             else
-                e = cudaMemsetAsync(s + (1 + a) * m, 0, m * 8, c->stream);
+                e = cudaMemsetAsync(s + (1 + a) * m, 0, m * 8, cs);
         }
         if (e == cudaSuccess && c->physics == LBM_PHYS_CGM)
-            e = cudaMemcpyAsync(s + 4 * m, phase + off, m * 8, cudaMemcpyDefault, c->stream);
+            e = cudaMemcpyAsync(s + 4 * m, phase + off, m * 8, cudaMemcpyDefault, cs);
         for (int a = 0; a < 3 && e == cudaSuccess && c->physics == LBM_PHYS_MHD; ++a) {
             if (B)
-                e = cudaMemcpyAsync(s + (5 + a) * m, B + a * n + off, m * 8, cudaMemcpyDefault, c->stream);
+                e = cudaMemcpyAsync(s + (5 + a) * m, B + a * n + off, m * 8, cudaMemcpyDefault, cs);
             else
-                e = cudaMemsetAsync(s + (5 + a) * m, 0, m * 8, c->stream);
+                e = cudaMemsetAsync(s + (5 + a) * m, 0, m * 8, cs);
         }
+        if (e == cudaSuccess) e = cudaEventRecord(c->slab_ready[b], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->slab_ready[b], 0);
         if (e == cudaSuccess) e = phys_init(c, s, z0, k, false);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_init_fields");
+        if (e == cudaSuccess) e = cudaEventRecord(c->slab_free[b], c->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(c->stream);
+        return cuda_fail(c, e, "lbm_init_fields");
     }
     c->have_prev = false;
-    cudaError_t e = cudaStreamSynchronize(c->stream);
+    e = cudaStreamSynchronize(c->stream);  // it waited for every slab's copies
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_init_fields");
     return LBM_OK;
 }
@@ -405,22 +440,33 @@ lbm_status lbm_fields(lbm_ctx* c, double* rho, double* u, double* phase, double*
     if (c->batch) return fail(c, LBM_ERR_ARG, "use the per-domain view of a batch (lbm_batch_domain)%s");
     const size_t n = c->box.n, plane = (size_t)c->box.nx * c->box.ny;
     const int nzs = slab_planes(c);
-    for (int z0 = 0; z0 < c->box.nz; z0 += nzs) {
+    // Two slabs in turn: the field kernel of slab j (the context's stream)
+    // overlaps the copies of slab j - 1 (copy stream).
+    cudaStream_t cs = c->copy_stream;
+    cudaError_t e = cudaSuccess;
+    for (int z0 = 0, j = 0; z0 < c->box.nz && e == cudaSuccess; z0 += nzs, ++j) {
         const int k = (z0 + nzs <= c->box.nz) ? nzs : c->box.nz - z0;
         const size_t m = plane * k, off = plane * z0;
-        double* s = c->staging;
-        cudaError_t e = phys_fields(c, s, z0, k);
-        if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho + off, s, m * 8, cudaMemcpyDefault, c->stream);
+        const int b = j & 1;
+        double* s = slab_buf(c, b);
+        if (j >= 2) e = cudaStreamWaitEvent(c->stream, c->slab_free[b], 0);  // slab j - 2 copied out
+        if (e == cudaSuccess) e = phys_fields(c, s, z0, k);
+        if (e == cudaSuccess) e = cudaEventRecord(c->slab_ready[b], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c->slab_ready[b], 0);
+        if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho + off, s, m * 8, cudaMemcpyDefault, cs);
         for (int a = 0; a < 3 && e == cudaSuccess && u; ++a)
-            e = cudaMemcpyAsync(u + a * n + off, s + (1 + a) * m, m * 8, cudaMemcpyDefault, c->stream);
+            e = cudaMemcpyAsync(u + a * n + off, s + (1 + a) * m, m * 8, cudaMemcpyDefault, cs);
         if (e == cudaSuccess && phase && (c->physics == LBM_PHYS_CGM || c->physics == LBM_PHYS_SC))
-            e = cudaMemcpyAsync(phase + off, s + 4 * m, m * 8, cudaMemcpyDefault, c->stream);
+            e = cudaMemcpyAsync(phase + off, s + 4 * m, m * 8, cudaMemcpyDefault, cs);
         for (int a = 0; a < 3 && e == cudaSuccess && B && c->physics == LBM_PHYS_MHD; ++a)
-            e = cudaMemcpyAsync(B + a * n + off, s + (5 + a) * m, m * 8, cudaMemcpyDefault, c->stream);
-        // the staging slab is reused by the next slab: order the copies first
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_fields");
+            e = cudaMemcpyAsync(B + a * n + off, s + (5 + a) * m, m * 8, cudaMemcpyDefault, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(c->slab_free[b], cs);
     }
+    // the caller's buffers are complete once the copy stream has drained
+    const cudaError_t e1 = cudaStreamSynchronize(cs);
+    const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_fields");
     return device_status(c);
 }
 

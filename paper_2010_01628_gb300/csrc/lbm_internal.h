@@ -32,8 +32,12 @@ struct lbm_ctx {
     int npartials;
     double* result;   // reduction result (device)
     double* result_host;
-    double* staging;  // FP64 field slab
+    double* staging;  // two FP64 field slabs of 8 planes x staging_cells, back to back
     size_t staging_cells;
+    cudaStream_t copy_stream = nullptr;  // host<->device field copies, overlapping the slab kernels
+    cudaEvent_t slab_ready[2] = {nullptr, nullptr};  // a slab's copies (upload) or kernel (download) done
+    cudaEvent_t slab_free[2] = {nullptr, nullptr};   // a slab's kernel (upload) or copies (download) done
+    cudaEvent_t fields_start = nullptr;              // orders the copy stream after earlier work
     lbm_alloc_fn alloc;
     lbm_free_fn release;
     void* user;
