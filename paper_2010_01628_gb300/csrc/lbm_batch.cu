@@ -128,11 +128,14 @@ __device__ __forceinline__ bool tile_node(const BatchDomain* __restrict__ doms, 
 // scratch (colour gradient only): phi of every domain's nodes, then rho_r,
 // each `scratch_n` values long; a domain's nodes start at its soff.  WALLS:
 // false when every domain is periodic in all three directions (the node code
-// then carries no bounce-back).  The FP32 colour-gradient variant is held to
-// 64 registers (4 CTAs of 256 per SM; its order-parameter pass waits on 68
-// loads per node and needs the warps).
+// then carries no bounce-back).  The FP32 colour-gradient and Shan-Chen
+// variants are held to 64 registers (4 CTAs of 256 or 8 of 128 per SM): their
+// first passes wait on the neighbours' loads and need the warps (Shan-Chen
+// sweep 19.0 -> 20.6 GLUPS against 96 registers; 48 for the colour gradient
+// was slower).
 template <int PHYS, typename S, typename C, bool WALLS>
-__global__ void __launch_bounds__(256, (PHYS == LBM_PHYS_CGM && sizeof(S) == 4) ? 4 : 1) batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
+__global__ void __launch_bounds__(256, ((PHYS == LBM_PHYS_CGM || PHYS == LBM_PHYS_SC) && sizeof(S) == 4) ? 4 : 1)
+    batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
                                                     uint32_t ntiles, long nsteps, int parity0, int dry,
                                                     BarrierState* bs, unsigned long long timeout_ns, C* scratch,
                                                     size_t scratch_n) {
