@@ -282,7 +282,12 @@ lbm_status lbm_get_launch_shape(const lbm_ctx *ctx, int *variant, int *threads, 
  * (rho - 1) * 30 and u * 10 (lid speed 0.1 -> 1).
  * Parameters (lbm_cnn_param_count of them): per layer, weights
  * [C_out][C_in][27] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)) then biases [C_out].
- * Fields are FP64 planar ([n] rho, [3n] u), host or device pointers. */
+ * Fields are FP64 planar ([n] rho, [3n] u), host or device pointers; device
+ * pointers of the current device are read in place (each call synchronises
+ * before it returns), host ones are copied in first.
+ * Errors: LBM_ERR_ARG for null handles or wrong counts, LBM_ERR_OOM, LBM_ERR_CUDA,
+ * LBM_ERR_TIMEOUT when a tensor-core pipeline wait ran past its bound (the
+ * kernels then drain and free their TMEM; the context stays usable). */
 typedef struct lbm_cnn lbm_cnn;
 size_t lbm_cnn_param_count(void);
 /* init_weights: NULL = deterministic He-uniform initialisation. */
