@@ -130,9 +130,9 @@ __device__ __forceinline__ bool tile_node(const BatchDomain* __restrict__ doms, 
 // false when every domain is periodic in all three directions (the node code
 // then carries no bounce-back).  The FP32 colour-gradient and Shan-Chen
 // variants are held to 64 registers (4 CTAs of 256 or 8 of 128 per SM): their
-// first passes wait on the neighbours' loads and need the warps (Shan-Chen
-// sweep 19.0 -> 20.6 GLUPS against 96 registers; 48 for the colour gradient
-// was slower).
+// first passes wait on the neighbours' loads and need the warps.  Measured on
+// the 64-domain sweeps: Shan-Chen 20.6 GLUPS at 64 registers, 19.0 at 96 and
+// 18.9 at 48; colour gradient 14.0 at 64, 13.7 at 80 and 12.3 at 48.
 template <int PHYS, typename S, typename C, bool WALLS>
 __global__ void __launch_bounds__(256, ((PHYS == LBM_PHYS_CGM || PHYS == LBM_PHYS_SC) && sizeof(S) == 4) ? 4 : 1)
     batch_kernel(S* bufA, S* bufB, const BatchDomain* __restrict__ doms, int nd,
