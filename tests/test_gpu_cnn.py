@@ -1,10 +1,12 @@
 """Warm-start network on the GPU (tcgen05 BF16 tensor-core kernels with TMEM
-accumulators and tensor-map TMA staging) against the FP64 numpy oracle, and
+accumulators; rows staged by bulk copies) against the FP64 numpy oracle, and
 the warm start's gain over a cold start.
 
-Shapes cover the tile boxes the kernels choose: 16 x 8 x 1 and 8 x 8 x 2 boxes
-on small ragged grids, and 128-voxel x-rows with a ragged second tile
-(nx = 130), where more CTAs than tiles leave some weight-gradient CTAs empty.
+Shapes cover the staging cases of the kernels: rows that fit one tile (nx <=
+128: halo cells zeroed once, cells past a short row left stale), rows of two
+tiles (nx = 130: halo cells written per row, a ragged second tile whose
+weight-gradient K-steps stop early), staged rows outside the grid at every
+y and z face, and more CTAs than tiles (empty weight-gradient CTAs).
 
 Tolerances: activations and kernel weights are BF16 (unit roundoff 2^-9 ~
 2e-3); four layers of rounded inputs, weights and activations put the output
