@@ -75,3 +75,23 @@ def test_features_layout():
     assert abs(f[0, 0, 0, 11] - np.cos(-0.75 * np.pi)) < 1e-15
     # r (y + 1)/2: r at the top node centre y = 2/3
     assert abs(f[0, 2, 0, 15] - 1.0 * (2.0 / 3.0 + 1.0) / 2.0) < 1e-15
+
+
+def test_receptive_field_is_nine_nodes():
+    """Four zero-padded 3x3x3 layers: an output depends on exactly the 9^3
+    inputs around it. The network run on that neighbourhood (clipped to the
+    grid) reproduces the full-grid output; on the 7^3 neighbourhood it does
+    not."""
+    n = 14
+    p = small_params(7)
+    X = C.features((n, n, n), 600.0)
+    full = C.forward(p, X)[-1]
+    for (x, y, z) in [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (7, 7, 7), (3, 6, n - 2)]:
+        for r, same in ((4, True), (3, False)):
+            lo = [max(c - r, 0) for c in (z, y, x)]
+            hi = [min(c + r + 1, n) for c in (z, y, x)]
+            out = C.forward(p, X[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])[-1][z - lo[0], y - lo[1], x - lo[2]]
+            if same:
+                np.testing.assert_array_equal(out, full[z, y, x])
+            else:
+                assert np.abs(out - full[z, y, x]).max() > 1e-8

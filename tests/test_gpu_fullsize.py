@@ -1,7 +1,8 @@
 """Parity at the full workload sizes, in the launch configurations the
 benchmark times: the 64-domain Hartmann batch and the 64-domain droplet
 (density-ratio) batch (one persistent graph-captured launch per call,
-autotuned shape) and the 256^3 colour-gradient droplets.
+autotuned shape), the 256^3 colour-gradient droplets and the warm-start
+network at 128^3.
 Outputs are checked on sampled domains or nodes the oracle can compute alone.
 """
 import numpy as np
@@ -133,3 +134,39 @@ def test_cgm_droplets_256_sampled():
         ref["phase"].append(o["phase"][r, r, r])
     for f in ("rho", "u", "phase"):
         assert rel_l2(got[f], ref[f]) <= 1e-5, f
+
+
+def test_cnn_forward_128_sampled():
+    """The warm-start network at the study's 128^3 grid with the committed
+    weights, as lbm_cnn_warm_start and the benchmark run it: outputs at
+    sampled nodes (corners, edges, faces, interior) against the FP64 numpy
+    network run on each node's receptive field, the 9^3 nodes around it
+    clipped to the grid. The clipped faces then carry the grid's own zero
+    padding, and the patch's other faces lie too far out to reach the centre
+    through four 3x3x3 layers. Bound: the BF16 forward bound, 3e-2."""
+    import os
+
+    from oracle import cnn_oracle as C
+    from paper_2010_01628_gb300 import binding as L
+    from paper_2010_01628_gb300 import surrogate as S
+    n, re = 128, 600.0
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    w, _ = S.load_weights(os.path.join(root, "paper_2010_01628_gb300", "weights", "cavity128_warmstart.npz"))
+    net = L.lbm_cnn_create((n, n, n), w)
+    try:
+        L.lbm_cnn_set_input(net, re)
+        got = L.lbm_cnn_forward(net, n ** 3).reshape(n, n, n, 4)  # [z][y][x][4]
+    finally:
+        L.lbm_cnn_destroy(net)
+    X = C.features((n, n, n), re)  # [z][y][x][16]
+    rng = np.random.default_rng(12)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 0, 64), (64, n - 1, 64), (3, 64, n - 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(6)]
+    g, r = [], []
+    for (x, y, z) in pts:
+        lo = [max(c - 4, 0) for c in (z, y, x)]
+        hi = [min(c + 5, n) for c in (z, y, x)]
+        out = C.forward(w.astype(np.float64), X[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]])[-1]
+        r.append(out[z - lo[0], y - lo[1], x - lo[2]])
+        g.append(got[z, y, x])
+    assert rel_l2(np.array(g), np.array(r)) < 3e-2
