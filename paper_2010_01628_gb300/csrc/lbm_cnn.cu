@@ -17,9 +17,9 @@
 //    per (dy, dz) the 130-node row (with its x-halo) of every channel chunk
 //    is staged by 1D bulk copies of its contiguous runs, and the three
 //    x-shifted taps read it through descriptor start offsets of 16 bytes
-//    (unswizzled core matrices): 9 staged rows per tile instead of 27 boxes.
-//    The same kernel runs the backward data pass with the flipped, transposed
-//    weights.
+//    (unswizzled core matrices): 9 staged rows per tile instead of 27 boxes,
+//    three rows per ring stage.  The same kernel runs the backward data pass
+//    with the flipped, transposed weights.
 //  - wgrad_tc: weight gradients on the tensor cores (rows x input channels as
 //    M at one x-shift, output channels as N, voxels as K) from the same nine
 //    staged rows per tile, with the bias gradients summed from the staged dY
@@ -62,12 +62,6 @@ struct Shape {
     long P;
 };
 
-__device__ __forceinline__ void tap_offset(int tap, int& dx, int& dy, int& dz) {
-    dx = tap % 3 - 1;
-    dy = (tap / 3) % 3 - 1;
-    dz = tap / 9 - 1;
-}
-
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 __device__ __forceinline__ uint32_t bf_pack(float a, float b) {
@@ -94,8 +88,11 @@ __device__ __forceinline__ uint32_t bf_pack(float a, float b) {
 // TMA's 64-byte (CI = 32) or 32-byte (CI = 16) swizzle and stay in shared
 // memory for the CTA's life.
 //
-// Roles (192 threads): warp 0 stages rows into a ring of NSTAGE buffers (lane
-// 0 waits and issues the copies, the warp writes the zero cells); warp 1
+// Roles (192 threads): warp 0 stages rows into a ring of NSTAGE stages of
+// three rows each, one hand-off per stage (lane 0 waits and arms the stage,
+// lanes 0 .. 3 CI/8 - 1 issue one row chunk's copy each, the warp writes the
+// zero cells; when a row is one tile its halo cells never change, so the ring
+// is zeroed once and only rows outside the grid are written over); warp 1
 // allocates TMEM and its lane 0 issues the MMAs (M = 128, N = CO, K = 16) into
 // one of two TMEM accumulators; warps 2-5 read the finished accumulator (each
 // warp its 32-lane quarter: one voxel per thread, CO columns), apply the
