@@ -77,3 +77,22 @@ def test_committed_weights_match_the_network():
     assert np.all(np.isfinite(w))
     assert meta["grid"] == 128 and meta["train_count"] == 512 and meta["heldout_count"] == 32
     assert meta["tol"] == 1e-6 and meta["reynolds_seed"] == 4
+
+
+def test_solver_judges_the_network():
+    """surrogate.judge: the prediction against the cold run's converged fields
+    (u against ||u_cold||, rho against ||rho_cold - 1||) and the warm run's
+    final fields against the cold run's."""
+    torch = pytest.importorskip("torch")
+    from paper_2010_01628_gb300 import surrogate as S
+    g = torch.Generator().manual_seed(0)
+    rc = 1.0 + 1e-3 * torch.randn(6, 5, 4, generator=g, dtype=torch.float64)
+    uc = 0.05 * torch.randn(3, 6, 5, 4, generator=g, dtype=torch.float64)
+    same = S.judge((rc, uc), (rc, uc), (rc, uc))
+    assert all(v == 0.0 for v in same.values())
+    # the rest state as a prediction: u error 1, rho error 1 (rho - 1 = 0 everywhere)
+    rest = S.judge((torch.ones_like(rc), torch.zeros_like(uc)), (rc, uc), (rc, uc))
+    assert abs(rest["net_err_u"] - 1.0) < 1e-15 and abs(rest["net_err_rho"] - 1.0) < 1e-15
+    # a warm run ending 1% off in u and 2% off in rho - 1
+    r = S.judge((rc, uc), (rc, uc), (1.0 + 1.02 * (rc - 1.0), 1.01 * uc))
+    assert abs(r["warm_vs_cold_u"] - 0.01) < 1e-12 and abs(r["warm_vs_cold_rho"] - 0.02) < 1e-9
